@@ -1,0 +1,255 @@
+"""Pins of the oracle's solver against results fixed independently of it.
+
+P2  homogeneous RVE, no damage: zero fluctuation, sigma = g C : f uniform, no CG iteration.
+P3  laminates with even layer widths (no Nyquist content): the exact 1D laminate solution
+    (normal load: Reuss 1/<1/M>; parallel load: closed form of the uniform-sigma_xx problem).
+P4  brute force: the unit-load equilibrium equals the minimiser of the elastic energy over
+    displacements assembled with dense DFT derivative matrices (numpy.linalg.lstsq); the damage
+    solve equals a dense direct solve of the same operator (numpy.linalg.solve).
+P5  crack-tip enrichment is a fixed point: a damage solve with H = psi_ini returns phi_ini, and
+    psi_ini vanishes away from the two tips (homogeneous Gc, A = I).
+P6  1D AT2 profile: with phi pinned to 1 at one voxel the damage solve approaches exp(-|x|/l)
+    and Gamma -> 1 as l/h grows (Sec. 2.1, Eqs. (CrackLenght), (CrackLenghtreal)).
+P7  uniform branch of a homogeneous uncracked RVE: phi = sqrt(2 l tau/(Gc V)),
+    H = Gc phi/(2 l (1-phi)), E = sqrt(H/psi1), Sigma = g(phi) M E, T by trapezoid.
+P8  without history the model is variational, so the external work V T^n equals the change of
+    E_mec + D + int g psi_ini up to the quadrature error of the load curve (Sec. 5.1: the two
+    toughness measures coincide without history); the gap vanishes as the increment shrinks.
+R   converged increments make the independently coded residuals R1, R2, R3 vanish.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import material as mat
+from oracle import residuals as res
+from oracle import solver as S
+
+RNG = np.random.default_rng(2)
+
+
+# ---- dense brute-force helpers (explicit DFT matrices, no FFT) ----------------------------------
+
+def _xi1d(n):
+    k = np.arange(n)
+    k = np.where(k > n // 2, k - n, k)
+    xi = 2 * np.pi * k / n
+    if n % 2 == 0:
+        xi[n // 2] = 0.0
+    return xi
+
+
+def _deriv1d(n):
+    j = np.arange(n)
+    F = np.exp(-2j * np.pi * np.outer(j, j) / n)
+    Finv = np.conj(F) / n
+    return np.real(Finv @ np.diag(1j * _xi1d(n)) @ F)
+
+
+def _deriv(shape, a):
+    nz, ny, nx = shape
+    mats = [np.eye(nz), np.eye(ny), np.eye(nx)]
+    mats[2 - a] = _deriv1d(shape[2 - a])
+    return np.kron(np.kron(mats[0], mats[1]), mats[2])
+
+
+def _micro_random(n, dim, n_grains=3, seed=5):
+    rng = np.random.default_rng(seed)
+    m = synth.voronoi(n, n_grains, seed, C=(1.0, 0.6, 0.5), orientation="inplane" if dim == 2 else "so3",
+                      beta=1.5, sigma_Gc=0.3)
+    m.C_cubic[0] = synth.iso_constants(3.0, 0.25)
+    return m
+
+
+@pytest.mark.parametrize("n,dim", [((8, 4), 2), ((4, 4, 2), 3)])
+def test_mech_solve_matches_dense_energy_minimiser(n, dim):
+    m = _micro_random(n, dim)
+    w = synth.Workload(m, ell=1.5)
+    p = S.Params(ell=1.5, f6=(0.2, 1.0, -0.3, 0.1, 0.05, 0.4), tol_mech=1e-14)
+    model = S.Model(m, p)
+    phi = RNG.uniform(0.0, 0.8, model.grid)
+    F1, _ = S.mech_solve(model, phi, np.zeros((dim, dim) + model.grid))
+    eps_cg = model.fB + 0.5 * (F1 + np.swapaxes(F1, 0, 1))
+    # dense: u (dim x N) -> eps = f + sym grad u; minimise sum 1/2 eps : C_phi : eps
+    N = int(np.prod(model.grid))
+    D = [_deriv(model.grid, a) for a in range(dim)]
+    B = np.zeros((dim * dim * N, dim * N))
+    for i in range(dim):
+        for j in range(dim):
+            row = (i * dim + j) * N
+            B[row:row + N, j * N:(j + 1) * N] += 0.5 * D[i]
+            B[row:row + N, i * N:(i + 1) * N] += 0.5 * D[j]
+    g = mat.degradation(phi, p.k_res).reshape(-1)
+    Cv = model.C.reshape(N, dim * dim, dim * dim) * g[:, None, None]
+    Cbig = np.zeros((dim * dim * N, dim * dim * N))
+    for a in range(dim * dim):
+        for b in range(dim * dim):
+            Cbig[a * N:(a + 1) * N, b * N:(b + 1) * N] = np.diag(Cv[:, a, b])
+    fvec = np.repeat(model.f.reshape(-1), N)
+    K = B.T @ Cbig @ B
+    u = np.linalg.lstsq(K, -B.T @ Cbig @ fvec, rcond=1e-13)[0]
+    eps_dense = (fvec + B @ u).reshape((dim, dim) + model.grid)
+    np.testing.assert_allclose(eps_cg, eps_dense, atol=1e-10)
+
+
+@pytest.mark.parametrize("n,dim", [((8, 8), 2), ((4, 4, 4), 3)])
+def test_damage_solve_matches_dense_direct_solve(n, dim):
+    m = _micro_random(n, dim)
+    p = S.Params(ell=1.7, tol_dmg=1e-14)
+    model = S.Model(m, p)
+    H = RNG.uniform(0.0, 3.0, model.grid)
+    phi, _ = S.damage_solve(model, H, np.zeros(model.grid))
+    N = int(np.prod(model.grid))
+    D = [_deriv(model.grid, a) for a in range(dim)]
+    a = (model.Gc / p.ell + 2 * H).reshape(-1)
+    L = np.diag(a)
+    for i in range(dim):
+        for j in range(dim):
+            L += D[i].T @ np.diag((model.Gc * p.ell * model.A[i, j]).reshape(-1)) @ D[j]
+    ref = np.linalg.solve(L, 2 * H.reshape(-1)).reshape(model.grid)
+    np.testing.assert_allclose(phi, ref, atol=1e-12)
+    # D(phi) by its definition with dense derivative matrices
+    gr = [(Di @ ref.reshape(-1)).reshape(model.grid) for Di in D]
+    quad = sum(model.A[i, j] * gr[i] * gr[j] for i in range(dim) for j in range(dim))
+    Dref = np.sum(model.Gc * (ref ** 2 / (2 * p.ell) + 0.5 * p.ell * quad))
+    assert abs(model.dissipation(phi) - Dref) < 1e-12 * Dref
+
+
+def test_homogeneous_no_damage_uniform_stress():
+    m = synth.homogeneous((16, 8), E=2.0, nu=0.25)
+    p = S.Params(ell=2.0, f6=(0.3, 1.0, 0.0, 0.0, 0.0, 0.2))
+    model = S.Model(m, p)
+    for phi in (np.zeros(model.grid), np.full(model.grid, 0.37)):
+        F1, it = S.mech_solve(model, phi, np.zeros((2, 2) + model.grid))
+        assert it == 0 and np.abs(F1).max() == 0.0
+        lam, mu = m.C_cubic[0, 1], m.C_cubic[0, 2]
+        f = model.f
+        sig_ref = mat.degradation(phi[0, 0, 0], p.k_res) * (lam * np.trace(f) * np.eye(2) + 2 * mu * f)
+        sig = model.stress(model.fB, phi)
+        np.testing.assert_allclose(sig, sig_ref.reshape(2, 2, 1, 1, 1) * np.ones_like(sig), rtol=1e-14)
+
+
+def test_laminate_reuss_and_parallel_closed_forms():
+    widths = [6, 10, 8, 8]
+    phases = [(1.0, 0.3, 1.0), (5.0, 0.2, 1.0), (2.0, 0.35, 1.0), (0.5, 0.3, 1.0)]
+    m = synth.laminate((32, 8), "x", widths, phases)
+    C = np.array([synth.iso_constants(E, nu) for (E, nu, _) in phases])
+    M_layer = np.repeat(C[:, 0], widths)
+    lam_layer = np.repeat(C[:, 1], widths)
+    # normal load (e_x (x) e_x): sigma_xx uniform = 1 / <1/M>  (Reuss)
+    model = S.Model(m, S.Params(ell=2.0, f6=(1, 0, 0, 0, 0, 0), k_res=0.0))
+    phi = np.zeros(model.grid)
+    F1, _ = S.mech_solve(model, phi, np.zeros((2, 2) + model.grid))
+    sig = model.stress(model.fB + 0.5 * (F1 + np.swapaxes(F1, 0, 1)), phi)
+    reuss = 1.0 / np.mean(1.0 / M_layer)
+    np.testing.assert_allclose(sig[0, 0], reuss, rtol=1e-12)
+    np.testing.assert_allclose(sig[0, 1], 0.0, atol=1e-12)
+    np.testing.assert_allclose(sig[1, 1][0, 0], lam_layer * reuss / M_layer, rtol=1e-12)
+    # parallel load (e_y (x) e_y): sigma_xx = c uniform, eps_xx = (c - lam)/M with <eps_xx> = 0
+    model = S.Model(m, S.Params(ell=2.0, f6=(0, 1, 0, 0, 0, 0), k_res=0.0))
+    F1, _ = S.mech_solve(model, phi, np.zeros((2, 2) + model.grid))
+    eps = model.fB + 0.5 * (F1 + np.swapaxes(F1, 0, 1))
+    sig = model.stress(eps, phi)
+    c = np.mean(lam_layer / M_layer) / np.mean(1.0 / M_layer)
+    exx = (c - lam_layer) / M_layer
+    np.testing.assert_allclose(eps[0, 0][0, 0], exx, atol=1e-12)
+    np.testing.assert_allclose(sig[0, 0], c, rtol=1e-12)
+    Syy = np.mean(lam_layer * exx + M_layer)
+    assert abs(S.macro_stress(model, sig) - Syy) < 1e-12 * Syy
+
+
+def test_cte_is_fixed_point_of_damage_solve():
+    crack = synth.Crack(synth.CRACK_CTE, row=16, x0=4, length=10, phi_M=0.8)
+    m = synth.homogeneous((32, 32), crack=crack)
+    model = S.Model(m, S.Params(ell=2.0, tol_dmg=1e-14))
+    st = S.init_state(model)
+    assert abs(st.phi.max() - 0.8) < 1e-15
+    phi, _ = S.damage_solve(model, st.psi_ini, np.zeros(model.grid))
+    np.testing.assert_allclose(phi, st.phi, atol=1e-12)
+    off = np.ones(model.grid, bool)
+    off[0, 16, 4] = off[0, 16, 13] = False
+    assert np.abs(st.psi_ini[off]).max() < 1e-12 * st.psi_ini.max()
+
+
+def test_at2_profile_and_unit_crack_surface():
+    """Continuum limit l/h -> infinity with n/l -> infinity (n = 8 l^2): the Nyquist-zeroed
+    gradient leaves the checkerboard mode unpenalised, so a point pin carries a (-1)^x component
+    of amplitude ~2 l/n that must vanish too."""
+    errs, gammas = [], []
+    for ell in (4.0, 8.0, 16.0, 32.0):
+        n = int(8 * ell * ell)
+        m = synth.homogeneous((n, 1))
+        model = S.Model(m, S.Params(ell=ell, tol_dmg=1e-14))
+        H = np.zeros(model.grid)
+        H[0, 0, 0] = 1e12
+        phi, _ = S.damage_solve(model, H, np.zeros(model.grid))
+        x = np.arange(n)
+        prof = np.exp(-np.minimum(x, n - x) / ell)
+        errs.append(np.abs(phi[0, 0] - prof).max())
+        gammas.append(abs(model.crack_surface(phi) - 1.0))
+    assert all(a > b for a, b in zip(errs, errs[1:])) and errs[-1] < 0.015
+    assert all(a > b for a, b in zip(gammas, gammas[1:])) and gammas[-1] < 0.002
+
+
+def _uniform_case(history=True, k=1e-6):
+    m = synth.homogeneous((8, 8), E=1.0, nu=0.3, Gc=1.0)
+    return S.Model(m, S.Params(ell=2.0, k_res=k, history=history, tol_root=1e-14))
+
+
+def test_uniform_branch_closed_form():
+    model = _uniform_case()
+    st = S.init_state(model)
+    assert st.tau == 0.0
+    V, Gc, ell, k = model.V, 1.0, 2.0, 1e-6
+    M = synth.iso_constants(1.0, 0.3)[0]
+    dtau = 0.05 * V
+    T, Sig0, E0 = 0.0, 0.0, 0.0
+    for n in range(1, 5):
+        st, _ = S.increment(model, st, dtau)
+        tau = n * dtau
+        phi = math.sqrt(2 * ell * tau / (Gc * V))
+        H = Gc * phi / (2 * ell * (1 - phi))
+        E = math.sqrt(H / (0.5 * M))
+        Sig = ((1 - phi) ** 2 + k) * M * E
+        T += 0.5 * (Sig + Sig0) * (E - E0)
+        Sig0, E0 = Sig, E
+        assert abs(st.phi.mean() - phi) < 1e-12 and np.ptp(st.phi) < 1e-12
+        assert abs(st.E - E) < 1e-11 * E
+        assert abs(st.Sigma - Sig) < 1e-11 * Sig
+        assert abs(st.T - T) < 1e-11 * T
+
+
+def test_no_history_energy_balance_second_order():
+    """Without history the damage equation g'(phi)(psi_o + psi_ini) + gamma_f' = 0 is the
+    stationarity of Psi = E_mec + D + int g(phi) psi_ini, so the external work V T equals the
+    change of Psi up to the trapezoid error."""
+    crack = synth.Crack(synth.CRACK_CTE, row=8, x0=0, length=4, phi_M=0.8)
+    m = synth.homogeneous((16, 16), crack=crack)
+    gaps, works = [], []
+    for steps, dtau in ((6, 0.2), (12, 0.1), (24, 0.05)):
+        model = S.Model(m, S.Params(ell=2.0, history=False, tol_stag=1e-11))
+        st = S.init_state(model)
+        k = model.p.k_res
+        psi0 = st.tau + float(np.sum(mat.degradation(st.phi, k) * st.psi_ini))
+        for _ in range(steps):
+            st, _ = S.increment(model, st, dtau)
+        rec = st.curve[-1]
+        psi = rec["Emec"] + rec["D"] + float(np.sum(mat.degradation(st.phi, k) * st.psi_ini))
+        gaps.append(model.V * st.T - (psi - psi0))
+        works.append(model.V * st.T)
+    # the gap is the quadrature error of the load curve: it vanishes at least linearly
+    assert gaps[0] / gaps[1] > 1.9 and gaps[1] / gaps[2] > 1.9, gaps
+    assert abs(gaps[2]) < 0.005 * works[2]
+
+
+def test_converged_increments_zero_residuals():
+    w = synth.small_cases()["fibre64x16"]
+    model = S.Model(w.micro, S.params_from_workload(w, tol_stag=1e-11))
+    st = S.init_state(model)
+    for _ in range(3):
+        H_prev = st.H
+        st, _ = S.increment(model, st, w.dtau)
+        r1, r2, r3 = res.check_state(model, st, H_prev)
+        assert r1 < 1e-10 and r2 < 1e-9 and r3 < 1e-11, (r1, r2, r3)
