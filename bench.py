@@ -1,0 +1,338 @@
+"""Benchmark of the FFT phase-field-fracture hot path on GB300.
+
+A step is one dissipation increment (the whole staggered solve: equilibrium CG, damage PCG,
+control root search, Anderson mixing, history and load-curve update) of the 512^2 fibre
+composite RVE (30% discs of radius 20, E_f/E_m = 5, Gc_f/Gc_m = 2, l = 3, central enriched
+crack of 64 voxels). Metric: voxel-updates/s = sum over (equilibrium-CG + damage-PCG iterations)
+x voxels, per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32r] [--impl reference]
+
+N > 1 runs one independent RVE replica per rank (the solve of one RVE does not shard; replicas
+only). Timing: W untimed increments, then K increments each bracketed by CUDA events on the
+library's stream; between timed increments L2 is flushed by writing 256 MiB; barrier +
+synchronize around the timed region, max over ranks. One JSON line on rank 0.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+WORKLOAD = "fibre_composite_512"
+
+
+def workload_desc():
+    return ("512x512 plane-strain fibre composite, RSA discs r=20 at 30% voxel fraction, E_f/E_m=5, "
+            "Gc_f/Gc_m=2, nu=0.3, l=3, k=1e-6, central CTE crack 64 voxels (phi_M=0.8), "
+            "dtau=1.5*Gc*A_g/300, f=e_y(x)e_y")
+
+
+def peaks():
+    try:
+        with open(MEASURED) as f:
+            m = json.load(f)
+        return m, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload(rank, precision):
+    import synth
+    w = synth.fibre_composite_512(seed=1 + rank)
+    w.precision = precision
+    return w
+
+
+def solver_tols(precision):
+    if precision == "fp64":
+        return dict(tol_stag=1e-8)
+    return dict(tol_mech=1e-6, tol_dmg=1e-6, tol_root=1e-7, tol_stag=1e-5)
+
+
+# ---- algorithmic work of the dominant kernel ----------------------------------------------------
+def axis_kernel_model(nx, ny, ns, word):
+    """Mechanics spectral pass (forward FFT along y, projection, inverse FFT) on one launch:
+    bytes = read + write of ns complex values per half-spectrum point; flops = 2 transforms x
+    5 log2(ny) per complex point and component + ~40 per point for the projection."""
+    import math
+    npts = (nx // 2 + 1) * ny
+    bytes_ = 2.0 * ns * npts * 2 * word
+    flops = npts * ns * 2 * 5 * math.log2(ny) + 40.0 * npts
+    return bytes_, flops
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2508_07424_gb300 import build, capi
+    from paper_2508_07424_gb300.rve import Rve
+    build.build()
+    stream = torch.cuda.current_stream()
+    w = make_workload(rank, args.precision)
+    tol = solver_tols(args.precision)
+    g = Rve.from_workload(w, stream=stream.cuda_stream, **tol)
+    N = g.nvox
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        g.step(w.dtau)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = g.launches()
+    g.timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    vu = 0
+    results = []
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        r = g.step(w.dtau)
+        ev[i][1].record(stream)
+        results.append(r)
+        vu += (r["mech_iters"] + r["dmg_iters"]) * N
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ax_ms, ax_n, ax_bytes = g.timing()
+    g.timing(False)
+    launches = g.launches() - launches0
+    clk = clocks.stop()
+    tot_ms = ms
+    tot_vu = vu
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        v = torch.tensor([float(vu)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(v, op=dist.ReduceOp.SUM)
+        tot_vu = float(v.item())
+
+    # e2e: the public C ABI from host buffers; every step uploads the microstructure, builds the
+    # enriched crack, runs one increment and reads back the result and the damage field.
+    e2e = None
+    if not args.no_e2e:
+        import numpy as np
+        e_steps = max(2, min(args.steps, 5))
+        m = w.micro
+        gid_host = torch.from_numpy(np.ascontiguousarray(m.grain_id)).pin_memory()
+        phi_host = torch.empty(N, dtype=torch.float64).pin_memory()
+        h2d = gid_host.numel() * 4 + m.C_cubic.nbytes + m.R.nbytes + m.Gc.nbytes + m.cleave_n.nbytes + m.beta.nbytes
+        d2h = N * 8 + 96
+        ge = Rve.from_workload(w, stream=stream.cuda_stream, **tol)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        evu = 0
+        for _ in range(e_steps):
+            m.grain_id = gid_host.numpy().reshape(m.grain_id.shape)
+            ge.set_microstructure(m)
+            r = ge.step(w.dtau)
+            phi_host.numpy()[:] = ge.get(capi.RVE_FIELD_PHI).reshape(-1)
+            evu += (r["mech_iters"] + r["dmg_iters"]) * N
+        torch.cuda.synchronize()
+        et = time.perf_counter() - t0
+        e2e = {"value": evu / et * world, "unit": "voxel-updates/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": e_steps,
+               "what": "set_microstructure from host arrays + enriched-crack setup + one increment + D2H of "
+                       "result and damage field, per step"}
+        ge.close()
+
+    if rank != 0:
+        return None
+    pk, src = peaks()
+    word = 8 if args.precision == "fp64" else 4
+    bytes_l, flops_l = axis_kernel_model(w.micro.n[0], w.micro.n[1], 3, word)
+    avg_s = ax_ms * 1e-3 / max(ax_n, 1)
+    if args.precision == "fp64":
+        peak = 152 * 2 * 2 * 2.07e9 / 1e12   # FP64: 2 DFMA/clk/SM (1.26 TFLOP/s), see the design doc
+        roof = {"kernel": "k_axis (mechanics: FFT_y + projection + inverse FFT_y)", "bound": "alu",
+                "achieved": flops_l / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops_l / avg_s / 1e12 / peak, "peak_source": "FP64 unit count x max SM clock",
+                "traffic": None, "avg_launch_us": avg_s * 1e6, "launches": ax_n}
+    else:
+        peak = pk["hbm_gbs"]
+        roof = {"kernel": "k_axis (mechanics: FFT_y + projection + inverse FFT_y)", "bound": "hbm",
+                "achieved": bytes_l / avg_s / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": bytes_l / avg_s / 1e9 / peak, "peak_source": src, "traffic": None,
+                "avg_launch_us": avg_s * 1e6, "launches": ax_n}
+    out = {
+        "metric": "FFT-PFF voxel-updates/s (fibre composite 512^2 increments)",
+        "value": tot_vu / (tot_ms * 1e-3),
+        "unit": "voxel-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "desc": workload_desc(), "precision": args.precision,
+                   "step": "one dissipation increment", "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas{world}"},
+        "increments": [{k: r[k] for k in ("n", "mech_iters", "dmg_iters", "stag_iters", "root_evals")} for r in results],
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "roofline": roof,
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(args, timed_steps=1)
+    return out
+
+
+def oracle_sample(rank=0, iters=60):
+    """A bounded sample of the same work in the FP64 NumPy oracle: ``iters`` equilibrium-CG
+    iterations at the initial state plus ``iters`` damage-PCG iterations at the first increment's
+    scale of E (each capped run stops at its iteration limit). Returns (voxel-updates, seconds)."""
+    import dataclasses
+
+    import numpy as np
+
+    from oracle import solver as S
+    w = make_workload(rank, "fp64")
+    p = S.params_from_workload(w)
+    model = S.Model(w.micro, dataclasses.replace(p, max_mech=iters, max_dmg=iters, tol_mech=1e-300, tol_dmg=1e-300))
+    st = S.init_state(model)
+    t0 = time.perf_counter()
+    try:
+        S.mech_solve(model, st.phi, st.F1)
+    except RuntimeError:
+        pass
+    t1 = time.perf_counter()
+    psi1 = np.full(model.grid, 0.5)
+    H = S.history_field(model, 0.05, psi1, st.psi_ini, st.H)
+    t2 = time.perf_counter()
+    try:
+        S.damage_solve(model, H, st.phi)
+    except RuntimeError:
+        pass
+    dt = (t1 - t0) + (time.perf_counter() - t2)
+    return 2 * iters * model.V, dt
+
+
+def cpu_baseline(args, timed_steps=1):
+    vu, dt = 0.0, 0.0
+    for _ in range(timed_steps):
+        a, b = oracle_sample()
+        vu += a
+        dt += b
+    return {"value": vu / dt, "unit": "voxel-updates/s", "cores": 1, "kind": "oracle",
+            "sample": "FP64 NumPy oracle on the same 512^2 RVE: 60 equilibrium-CG + 60 damage-PCG iterations; "
+                      "numpy.fft and einsum run single-threaded"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    for _ in range(args.warmup):
+        oracle_sample()
+    vu, dt = 0.0, 0.0
+    for _ in range(args.steps):
+        a, b = oracle_sample()
+        vu += a
+        dt += b
+    val = vu / dt
+    return {"impl": "reference", "metric": "FFT-PFF voxel-updates/s (fibre composite 512^2 increments)",
+            "value": val, "unit": "voxel-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "desc": workload_desc(), "precision": "fp64",
+                       "step": "60 equilibrium-CG + 60 damage-PCG iterations of the oracle on the same RVE"},
+            "cpu_baseline": {"value": val, "unit": "voxel-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": "60 equilibrium-CG + 60 damage-PCG oracle iterations per step"},
+            "e2e": {"value": val, "unit": "voxel-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32r"])
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    out = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

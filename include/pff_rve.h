@@ -1,0 +1,183 @@
+/*
+ * pff_rve.h -- C ABI of the GB300 (sm_103a) FFT phase-field-fracture RVE library.
+ *
+ * Method: effective toughness by FFT phase-field fracture under dissipation control
+ * (Aranda & Segurado, arXiv 2508.07424). One RVE handle owns the device state of one periodic
+ * voxel RVE: strain fluctuation, damage phi, history H, crack-tip-enrichment energy psi_ini, the
+ * load factor E and the load curve. Every step of an increment runs in the library's CUDA kernels;
+ * the host only drives scalar control (load-factor search, Anderson weights, stopping tests).
+ *
+ * Conventions
+ *   - Voxel grid n[0] x n[1] x n[2] (nx, ny, nz), voxel size h = 1; 2D problems use dim = 2,
+ *     nz = 1 and plane strain. Each used extent is a power of two in [4, 1024].
+ *   - Host field buffers are row-major with x fastest: index = x + nx (y + ny z).
+ *   - Symmetric tensors (strain, stress, the load direction f) are passed as the six tensor
+ *     components (xx, yy, zz, yz, xz, xy) -- shear NOT doubled. 2D fields carry (xx, yy, xy).
+ *   - All functions return an int status (RVE_OK = 0, negative on error). Calls on one handle
+ *     are stream-ordered on the handle's CUDA stream; use one host thread per handle.
+ *   - Ownership: the library copies every input buffer; the caller keeps ownership of its
+ *     pointers. Device memory belongs to the handle and is released by rve_destroy.
+ */
+#ifndef PFF_RVE_H
+#define PFF_RVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rve_s *rve_handle;
+
+enum rve_status {
+    RVE_OK = 0,
+    RVE_EINVAL = -1,        /* bad argument: size, NULL pointer, unsupported combination */
+    RVE_ENOMEM = -2,        /* device allocation failed */
+    RVE_ESTATE = -3,        /* call out of order (e.g. step before set_microstructure) */
+    RVE_ENOCONV = -4,       /* an iteration hit its cap; the handle rolls back to the last increment */
+    RVE_ENOROOT = -5,       /* the dissipation constraint could not be bracketed */
+    RVE_ETIMEOUT = -6,      /* a device-side wait gave up */
+    RVE_ENOTFRACTURED = -7, /* effective_toughness before the fracture point was reached */
+    RVE_ECUDA = -8,         /* a CUDA runtime call failed */
+    RVE_EBREAKDOWN = -9,    /* CG breakdown (non-positive curvature) or a non-finite scalar */
+};
+
+enum { RVE_SPLIT_NONE = 0, RVE_SPLIT_SPECTRAL = 1 };
+enum { RVE_FP64 = 0, RVE_FP32R = 1 };
+enum { RVE_CRACK_NONE = 0, RVE_CRACK_CTE = 1, RVE_CRACK_CPFE = 2 };
+
+/* Field identifiers for rve_get_field / rve_set_field. Sizes are n_vox doubles for scalar
+ * fields and ns * n_vox for tensor fields (ns = 3 in 2D, 6 in 3D; component-major, tensor
+ * components as above). */
+enum {
+    RVE_FIELD_PHI = 0,      /* committed damage phi                                     */
+    RVE_FIELD_H = 1,        /* committed history H (Eq. (HistoryNumIni))                 */
+    RVE_FIELD_PSI_INI = 2,  /* crack-tip enrichment energy psi_ini (Eq. (Enini))         */
+    RVE_FIELD_EPS = 3,      /* committed total strain E (f + eps~1)            [tensor]  */
+    RVE_FIELD_SIGMA = 4,    /* committed stress sigma = g(phi) C^r : eps       [tensor]  */
+    RVE_FIELD_FLUCT1 = 5,   /* unit-load strain fluctuation eps~1              [tensor]  */
+    RVE_FIELD_PSI1 = 6,     /* unit-load driving energy psi_o(f + eps~1)                 */
+    RVE_FIELD_PHI_TRIAL = 7 /* output of the last damage solve (rve_damage_solve)        */
+};
+
+/* Solver configuration (rve_config_default fills every field). */
+typedef struct {
+    int dim;               /* 2 (plane strain) or 3 */
+    int n[3];              /* grid; n[2] = 1 when dim = 2 */
+    double ell;            /* phase-field length l in voxels (Eq. (CrackLenght)) */
+    double k_res;          /* residual stiffness k of g(phi) = (1 - phi)^2 + k (Sec. 2.1) */
+    int split;             /* RVE_SPLIT_NONE (the paper's psi_o) or RVE_SPLIT_SPECTRAL */
+    int precision;         /* RVE_FP64 or RVE_FP32R */
+    int history;           /* 1: H = max(psi + psi_ini, H^n) (Eq. (HistoryNumIni)); 0: no history */
+    double f[6];           /* load direction f of E_M = f E (Eq. (f_defintion)); default e_y (x) e_y */
+    double tol_mech;       /* equilibrium: |P[sigma]| <= tol_mech |g C : f| */
+    double tol_dmg;        /* damage CG: |r| <= tol_dmg |2H| */
+    double tol_root;       /* control: |D - tau| <= tol_root tau */
+    double tol_stag;       /* staggered fixed point: the three ratios of Eq. (errors_crack) */
+    int max_mech_iters, max_dmg_iters, max_root_evals, max_stag_iters;
+    int anderson_m;        /* Anderson memory of the staggered iteration (0 = plain) */
+    double fracture_ratio; /* fracture point F: Sigma^F <= ratio * max Sigma (Sec. 4.2) */
+    void *stream;          /* cudaStream_t to run on; NULL: the handle creates its own */
+} rve_config;
+
+/* Microstructure (Sec. 2.2, Sec. 4.3). All pointers are host pointers, copied. */
+typedef struct {
+    const int32_t *grain_id; /* [n_vox] grain of each voxel, 0 <= id < n_grains */
+    int n_grains;
+    const double *C_cubic;   /* [n_grains][3] lattice C1111, C1122, C1212 (tensor constants) */
+    const double *R;         /* [n_grains][9] row-major rotation lattice -> sample (Eq. (Crot)) */
+    const double *Gc;        /* [n_grains] local toughness Gc (Eq. (CrackLenght)) */
+    const double *cleave_n;  /* [n_grains][3] weak-plane normal in lattice axes, or NULL */
+    const double *beta;      /* [n_grains] cleavage weight of Eq. (PFFani), or NULL (= 0) */
+    int crack_kind;          /* RVE_CRACK_NONE / _CTE (tips) / _CPFE (whole crack), Sec. 4.3 */
+    int crack_row;           /* crack voxels: y = crack_row, x = crack_x0 .. crack_x0+crack_len-1 */
+    int crack_x0, crack_len; /* (periodic in x; all z in 3D)                                    */
+    double crack_phi_M;      /* phi_M of Eq. (damini) */
+    double crack_stiffness;  /* stiffness multiplier of the crack voxels ("negligible stiffness") */
+} rve_micro;
+
+/* Result of one dissipation increment (Sec. 4.1-4.2). */
+typedef struct {
+    int n;              /* increment index (1-based) */
+    double E;           /* load factor E^n of E_M = f E */
+    double Sigma;       /* Sigma^n = <sigma> : f */
+    double D;           /* dissipation functional D(phi^n) (Eq. (CrackLenght_ani)) */
+    double Emec;        /* elastic energy E_mec (Eq. (elas_Ener_rot)) */
+    double T;           /* load-curve area T^n (Eq. (ABC)), per unit volume */
+    double Gamma;       /* crack surface Gamma(phi^n) (Eq. (CrackLenghtreal)) */
+    double tau;         /* prescribed dissipation tau^n */
+    int mech_iters, dmg_iters, root_evals, stag_iters;
+    int fractured;      /* 1 once Sigma^n <= fracture_ratio * max Sigma */
+    double stag_err;    /* final staggered error of Eq. (errors_crack) */
+} rve_step_result;
+
+/* Committed scalar state (for checkpoints and state injection in tests). */
+typedef struct {
+    int n;
+    double E, tau, T, Sigma, Sigma_max, tau0;
+    int fractured;
+} rve_scalars;
+
+void rve_config_default(rve_config *cfg);
+
+/* Allocate the device state of one RVE. cfg is copied. Errors: RVE_EINVAL (grid not a power of
+ * two in [4, 1024], dim/nz mismatch, ell <= 0, unsupported precision), RVE_ENOMEM, RVE_ECUDA. */
+int rve_create(const rve_config *cfg, rve_handle *out);
+
+/* Upload the microstructure and build the per-grain tables: rotated stiffness C^r (Eq. (Crot)),
+ * toughness Gc and cleavage tensor A_f (Eq. (PFFani)); crack voxels take crack_stiffness x C.
+ * Then build the enriched initial crack (Eqs. (damini)/(daminiAni), (Enini)): phi_ini, psi_ini,
+ * H^0 = psi_ini, tau^0 = D(phi_ini), E = Sigma = T = 0. Resets the load curve.
+ * Errors: RVE_EINVAL (ids out of range, split with a non-isotropic grain), RVE_ECUDA. */
+int set_microstructure(rve_handle h, const rve_micro *m);
+
+/* One increment at constant dissipation rate: tau^n = tau^{n-1} + dtau, then the staggered
+ * solve of Eq. (SystemDisany) -- Fourier-Galerkin CG equilibrium at unit load, the smallest
+ * E >= 0 with D(phi(E)) = tau^n, FFT-preconditioned CG for phi -- until the stopping test of
+ * Eq. (errors_crack); then the history update, Sigma, E_mec and the trapezoid T^n (Eq. (ABC)).
+ * out may be NULL. On RVE_ENOCONV / RVE_ENOROOT / RVE_EBREAKDOWN the committed state is left as
+ * it was before the call. */
+int step_dissipation(rve_handle h, double dtau, rve_step_result *out);
+
+/* Effective toughness of Eqs. (JaviGc)/(ABC): G = V / A_g (T^F - 1/2 Sigma^F E^F), V = voxel
+ * count, A_g = (nx - crack_len) (x nz in 3D). RVE_ENOTFRACTURED until the fracture point. */
+int effective_toughness(rve_handle h, double *g_eff);
+
+/* Copy a device field to / from a host buffer of n doubles (see RVE_FIELD_*). Setting PHI, H or
+ * FLUCT1 lets a caller inject a committed state; setting PHI also copies it to the trial field. */
+int rve_get_field(rve_handle h, int field, double *host, size_t n);
+int rve_set_field(rve_handle h, int field, const double *host, size_t n);
+int rve_get_scalars(rve_handle h, rve_scalars *s);
+int rve_set_scalars(rve_handle h, const rve_scalars *s);
+
+/* Single steps of the increment, for step-level checks against a reference:
+ *  rve_mech_solve:   unit-load equilibrium (Eq. (GFourier)) at the committed phi -> FLUCT1, PSI1.
+ *  rve_damage_solve: phi(E) of (Gc/l + 2 H_E) phi - div(Gc l A grad phi) = 2 H_E with
+ *                    H_E = max(E^2 psi1 + psi_ini, H) (Eqs. (SystemDisanyb), (HistoryNumIni)),
+ *                    warm-started from PHI_TRIAL; writes PHI_TRIAL and returns D(phi(E)).
+ *  rve_dissipation:  D and Gamma of a host damage field (Eqs. (CrackLenght_ani), (CrackLenghtreal)). */
+int rve_mech_solve(rve_handle h, int *iters);
+int rve_damage_solve(rve_handle h, double E, double *D, int *iters);
+int rve_dissipation(rve_handle h, const double *phi_host, double *D, double *Gamma);
+
+/* Checkpoint: serialise the committed state (fields + scalars + curve) to a host buffer.
+ * Call with buf = NULL to query the size in *len. rve_load restores it bit-exactly. */
+int rve_save(rve_handle h, void *buf, size_t *len);
+int rve_load(rve_handle h, const void *buf, size_t len);
+
+/* Per-kernel device timing (CUDA events around every launch of the named kernel class while
+ * enabled). kind: 0 = mechanics spectral pass (the y/z-axis FFT + projection kernel). */
+int rve_timing_enable(rve_handle h, int on);
+int rve_timing_get(rve_handle h, int kind, double *total_ms, long *launches, double *bytes_per_launch);
+
+/* Number of kernels this handle launched so far. */
+long rve_launch_count(rve_handle h);
+
+int rve_destroy(rve_handle h);
+const char *rve_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFF_RVE_H */

@@ -1,0 +1,1445 @@
+// Engine and C ABI of the FFT phase-field-fracture RVE library (sm_103a).
+//
+// One handle = one periodic voxel RVE resident on the device. An increment (Sec. 4.1) is the
+// staggered fixed point of Eq. (SystemDisany):
+//   1. equilibrium at unit load, Fourier-Galerkin CG (Eq. (GFourier)) on the strain fluctuation;
+//   2. the load factor E >= 0 with D(phi(E)) = tau^n (Eq. (SystemDisanyc)); each evaluation is an
+//      FFT-preconditioned CG solve of (Gc/l + 2 H_E) phi - div(Gc l A grad phi) = 2 H_E
+//      (Eqs. (SystemDisanyb), (gamFunct), (HistoryNumIni));
+//   3. Anderson mixing of the staggered map phi -> phi(E) (the accelerated staggering of Storvik
+//      et al., cited in Sec. 4.1), stopped by the three ratios of Eq. (errors_crack).
+// Every field operation runs in the kernels of pff_kernels.cuh / pff_functors.cuh; the host
+// keeps only scalar control: the bracketed Illinois search on E, the m x m Anderson
+// least-squares problem and the stopping tests.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/pff_rve.h"
+#include "pff_common.cuh"
+#include "pff_functors.cuh"
+#include "pff_kernels.cuh"
+
+using namespace pff;
+
+namespace pffeng {
+
+struct CudaError {
+    cudaError_t e;
+    const char *what;
+};
+struct StatusError {
+    int code;
+    std::string msg;
+};
+
+#define CK(call)                                                         \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) throw CudaError{e_, #call};               \
+    } while (0)
+
+thread_local std::string g_last_error;
+
+// ------------------------------------------------------------------------------------------------
+// Setup kernels
+// ------------------------------------------------------------------------------------------------
+
+// Per-grain tables. Grains [0, G) are the material grains, [G, 2G) their crack-voxel copies with
+// stiffness x crack_mult. Rotated cubic stiffness (Eq. (Crot)) in closed form:
+//   C^r_ijkl = C12 d_ij d_kl + C44 (d_ik d_jl + d_il d_jk) + (C11 - C12 - 2 C44) sum_m R_im R_jm R_km R_lm,
+// the isotropic part being rotation invariant. Cleavage tensor A = I + beta (I - n n), n the rotated
+// weak-plane normal, projected on the plane in 2D (Eq. (PFFani)).
+template <typename T>
+__global__ void k_build_tables(int G, int dim, const double *Cc, const double *R, const double *Gc,
+                               const double *cn, const double *beta, double ell, double crack_mult, T *Cm,
+                               T *acoef, T *Ktab, T *GcTab, T *Atab, T *acoefC, T *KtabC, T *lam, T *mu) {
+    int gg = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gg >= 2 * G) return;
+    const int g0 = gg % G;
+    const double mult = gg >= G ? crack_mult : 1.0;
+    const double c11 = Cc[3 * g0], c12 = Cc[3 * g0 + 1], c44 = Cc[3 * g0 + 2];
+    const double dl = c11 - c12 - 2.0 * c44;
+    const double *Rg = R + 9 * g0;
+    const int NS = dim == 2 ? 3 : 6;
+    const int ii3[6] = {0, 1, 2, 1, 0, 0}, jj3[6] = {0, 1, 2, 2, 2, 1};
+    const int ii2[3] = {0, 1, 0}, jj2[3] = {0, 1, 1};
+    const double sq2 = 1.41421356237309504880;
+    auto Cr = [&](int i, int j, int k, int l) {
+        double v = c12 * (i == j) * (k == l) + c44 * ((i == k) * (j == l) + (i == l) * (j == k));
+        for (int m = 0; m < 3; ++m) v += dl * Rg[3 * i + m] * Rg[3 * j + m] * Rg[3 * k + m] * Rg[3 * l + m];
+        return v;
+    };
+    for (int a = 0; a < NS; ++a) {
+        const int i = dim == 2 ? ii2[a] : ii3[a], j = dim == 2 ? jj2[a] : jj3[a];
+        const double wa = (i == j) ? 1.0 : sq2;
+        for (int b = 0; b < NS; ++b) {
+            const int k = dim == 2 ? ii2[b] : ii3[b], l = dim == 2 ? jj2[b] : jj3[b];
+            const double wb = (k == l) ? 1.0 : sq2;
+            Cm[(size_t)gg * NS * NS + a * NS + b] = (T)(mult * wa * wb * Cr(i, j, k, l));
+        }
+    }
+    // cleavage tensor
+    double n[3] = {1.0, 0.0, 0.0};
+    const double *nl = cn ? cn + 3 * g0 : n;
+    double nr[3];
+    for (int i = 0; i < 3; ++i) nr[i] = Rg[3 * i] * nl[0] + Rg[3 * i + 1] * nl[1] + Rg[3 * i + 2] * nl[2];
+    const double be = beta ? beta[g0] : 0.0;
+    double A[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) A[i][j] = (i == j) + be * ((i == j) - nr[i] * nr[j]);
+    double As[6];
+    if (dim == 2) { As[0] = A[0][0]; As[1] = A[1][1]; As[2] = A[0][1]; As[3] = As[4] = As[5] = 0.0; }
+    else { As[0] = A[0][0]; As[1] = A[1][1]; As[2] = A[2][2]; As[3] = A[1][2]; As[4] = A[0][2]; As[5] = A[0][1]; }
+    const double gc = Gc[g0];
+    for (int s = 0; s < 6; ++s) {
+        Atab[(size_t)gg * 6 + s] = (T)As[s];
+        Ktab[(size_t)gg * 6 + s] = (T)(gc * ell * As[s]);
+        KtabC[(size_t)gg * 6 + s] = (T)(ell * ell * As[s]);
+    }
+    acoef[gg] = (T)(gc / ell);
+    acoefC[gg] = (T)1.0;
+    GcTab[gg] = (T)gc;
+    lam[gg] = (T)(mult * c12);
+    mu[gg] = (T)(mult * c44);
+}
+
+__global__ void k_crack_setup(long long N, int nx, int ny, const int *gid0, int G, int kind, int row, int x0,
+                              int len, int *gid, double *phi_disc) {
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= N) return;
+    const int x = (int)(v % nx);
+    const int y = (int)((v / nx) % ny);
+    int g = gid0[v];
+    double pd = 0.0;
+    if (kind != RVE_CRACK_NONE && len > 0 && y == row) {
+        const int rel = ((x - x0) % nx + nx) % nx;
+        if (rel < len) {
+            g += G;
+            if (kind == RVE_CRACK_CPFE) pd = 1.0;
+            else if (rel == 0 || rel == len - 1) pd = 1.0;
+        }
+    }
+    gid[v] = g;
+    phi_disc[v] = pd;
+}
+
+__global__ void k_init_scal(Scal *sc, double tol2, int max_iters, double abar, double bbar) {
+    sc->done = 0; sc->flag = 0; sc->iters = 0; sc->first = 1; sc->max_iters = max_iters;
+    sc->tol2 = tol2; sc->beta = 0.0; sc->alpha = 0.0; sc->counter = 0u; sc->abar = abar; sc->bbar = bbar;
+}
+
+// ---- pointwise functors used by the engine ------------------------------------------------------
+template <typename T>
+struct PwSetupMeans {  // mean acoef, mean trace(Ktab)/d, mean trace(KtabC)/d
+    static constexpr int NR = 3;
+    static constexpr bool MAXRED = false;
+    bool skip_if_done;
+    const int *gid;
+    const T *acoef, *Ktab, *KtabC;
+    int dim;
+    __device__ void apply(long long v, double *acc) const {
+        const int g = gid[v];
+        acc[0] += (double)acoef[g];
+        const T *K = Ktab + (size_t)g * 6, *Kc = KtabC + (size_t)g * 6;
+        double tk = (double)K[0] + (double)K[1] + (dim == 3 ? (double)K[2] : 0.0);
+        double tc = (double)Kc[0] + (double)Kc[1] + (dim == 3 ? (double)Kc[2] : 0.0);
+        acc[1] += tk / dim;
+        acc[2] += tc / dim;
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const { sc->red[0] = t[0]; sc->red[1] = t[1]; sc->red[2] = t[2]; }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+template <typename T>
+struct PwMax {
+    static constexpr int NR = 1;
+    static constexpr bool MAXRED = true;
+    bool skip_if_done;
+    const T *f;
+    __device__ void apply(long long v, double *acc) const { acc[0] = fmax(acc[0], (double)f[v]); }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const { sc->red[0] = t[0]; }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+template <typename T>
+struct PwScaleCopy {  // out = s * in
+    static constexpr int NR = 0;
+    static constexpr bool MAXRED = false;
+    bool skip_if_done;
+    const T *in;
+    T *out;
+    double s;
+    __device__ void apply(long long v, double *) const { out[v] = (T)(s * (double)in[v]); }
+    struct Fin { __device__ void operator()(const double *) const {} };
+    __device__ Fin fin(Scal *) const { return Fin{}; }
+};
+
+template <typename T>
+struct PwPsiIni {  // psi_ini = max(0, -gamma'/g'(phi)) = max(0, gamma' / (2 (1 - phi)))  (Eq. (Enini))
+    static constexpr int NR = 0;
+    static constexpr bool MAXRED = false;
+    bool skip_if_done;
+    const T *gp, *phi;
+    T *psi_ini, *H;
+    __device__ void apply(long long v, double *) const {
+        const double val = (double)gp[v] / (2.0 * (1.0 - (double)phi[v]));
+        const T r = (T)(val > 0.0 ? val : 0.0);
+        psi_ini[v] = r;
+        H[v] = r;
+    }
+    struct Fin { __device__ void operator()(const double *) const {} };
+    __device__ Fin fin(Scal *) const { return Fin{}; }
+};
+
+// Staggered error on the strain: eps = E (f + x) against the previous iterate (tracking copy).
+template <typename T, int NS>
+struct PwStagEps {
+    static constexpr int NR = 2;
+    static constexpr bool MAXRED = false;
+    bool skip_if_done;
+    const T *x;
+    double *eps_it;
+    double f[NS];
+    double E;
+    long long N;
+    __device__ void apply(long long v, double *acc) const {
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+            const size_t i = a * N + v;
+            const double e = E * (f[a] + (double)x[i]);
+            const double d = e - eps_it[i];
+            acc[0] += d * d;
+            acc[1] += e * e;
+            eps_it[i] = e;
+        }
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const { sc->red[0] = t[0]; sc->red[1] = t[1]; }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+template <typename T>
+struct PwStagPhi {
+    static constexpr int NR = 2;
+    static constexpr bool MAXRED = false;
+    bool skip_if_done;
+    const T *pn, *p;
+    __device__ void apply(long long v, double *acc) const {
+        const double a = (double)pn[v], d = a - (double)p[v];
+        acc[0] += d * d;
+        acc[1] += a * a;
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const { sc->red[2] = t[0]; sc->red[3] = t[1]; }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+// Committed macroscopic stress Sigma = <sigma> : f and E_mec = sum g(phi) E^2 psi1.
+template <typename T, int NS>
+struct PwCommit {
+    static constexpr int NR = 2;
+    static constexpr bool MAXRED = false;
+    bool skip_if_done;
+    const T *Cm, *x, *phi, *psi1;
+    const int *gid;
+    double f[NS];
+    double E, k;
+    long long N;
+    __device__ void apply(long long v, double *acc) const {
+        const T *C = Cm + (size_t)gid[v] * NS * NS;
+        double u[NS];
+#pragma unroll
+        for (int a = 0; a < NS; ++a) u[a] = f[a] + (double)x[a * N + v];
+        const double ph = (double)phi[v];
+        const double gp = (1.0 - ph) * (1.0 - ph) + k;
+        double sf = 0.0;
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+            double s = 0.0;
+#pragma unroll
+            for (int b = 0; b < NS; ++b) s += (double)C[a * NS + b] * u[b];
+            sf += s * f[a];
+        }
+        acc[0] += gp * E * sf;
+        acc[1] += gp * E * E * (double)psi1[v];
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const { sc->red[4] = t[0]; sc->red[5] = t[1]; }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+// Anderson: Gram matrix of the residual differences dF_a = R_{a+1} - R_a (R_j = G_j - X_j) and
+// their products with the newest residual, K <= 5 columns.
+struct AAPtrs {
+    const double *X[6];
+    const double *G[6];
+};
+
+template <typename T>
+struct PwAAGram {
+    static constexpr int NR = 20;
+    static constexpr bool MAXRED = false;
+    bool skip_if_done;
+    AAPtrs h;
+    int K;  // number of differences (history length - 1)
+    __device__ void apply(long long v, double *acc) const {
+        double R[6];
+        for (int j = 0; j <= K; ++j) R[j] = h.G[j][v] - h.X[j][v];
+        double dF[5];
+        for (int a = 0; a < K; ++a) dF[a] = R[a + 1] - R[a];
+        int idx = 0;
+#pragma unroll
+        for (int a = 0; a < 5; ++a)
+#pragma unroll
+            for (int b = a; b < 5; ++b) {
+                if (a < K && b < K) acc[idx] += dF[a] * dF[b];
+                ++idx;
+            }
+#pragma unroll
+        for (int a = 0; a < 5; ++a)
+            if (a < K) acc[15 + a] += dF[a] * R[K];
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const {
+            for (int i = 0; i < 20; ++i) sc->red[i] = t[i];
+        }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+template <typename T>
+struct PwAAMix {  // phi = G_K - sum_a gamma_a (G_{a+1} - G_a)
+    static constexpr int NR = 0;
+    static constexpr bool MAXRED = false;
+    bool skip_if_done;
+    AAPtrs h;
+    int K;
+    double gam[5];
+    T *out;
+    __device__ void apply(long long v, double *) const {
+        double r = h.G[K][v];
+        for (int a = 0; a < K; ++a) r -= gam[a] * (h.G[a + 1][v] - h.G[a][v]);
+        out[v] = (T)r;
+    }
+    struct Fin { __device__ void operator()(const double *) const {} };
+    __device__ Fin fin(Scal *) const { return Fin{}; }
+};
+
+// Tensor-component conversion (xx, yy, zz, yz, xz, xy) <-> Mandel, and stress evaluation.
+template <typename T>
+__global__ void k_mandel_to_tensor(long long N, int dim, const T *src, double scale, const double *f, double *dst) {
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= N) return;
+    const double r2 = 0.70710678118654752440;
+    if (dim == 2) {
+        dst[0 * N + v] = scale * ((f ? f[0] : 0.0) + (double)src[0 * N + v]);
+        dst[1 * N + v] = scale * ((f ? f[1] : 0.0) + (double)src[1 * N + v]);
+        dst[2 * N + v] = scale * ((f ? f[2] : 0.0) + (double)src[2 * N + v]) * r2;
+    } else {
+        for (int a = 0; a < 6; ++a)
+            dst[a * N + v] = scale * ((f ? f[a] : 0.0) + (double)src[a * N + v]) * (a < 3 ? 1.0 : r2);
+    }
+}
+
+template <typename T>
+__global__ void k_tensor_to_mandel(long long N, int dim, const double *src, T *dst) {
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= N) return;
+    const double s2 = 1.41421356237309504880;
+    const int NS = dim == 2 ? 3 : 6;
+    for (int a = 0; a < NS; ++a) dst[a * N + v] = (T)(src[a * N + v] * (a < (dim == 2 ? 2 : 3) ? 1.0 : s2));
+}
+
+template <typename T>
+__global__ void k_stress(long long N, int dim, const T *Cm, const int *gid, const T *phi, double k, const double *eps,
+                         double *sig) {
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= N) return;
+    const int NS = dim == 2 ? 3 : 6;
+    const T *C = Cm + (size_t)gid[v] * NS * NS;
+    const double ph = (double)phi[v];
+    const double gp = (1.0 - ph) * (1.0 - ph) + k;
+    for (int a = 0; a < NS; ++a) {
+        double s = 0.0;
+        for (int b = 0; b < NS; ++b) s += (double)C[a * NS + b] * eps[b * N + v];
+        sig[a * N + v] = gp * s;
+    }
+}
+
+template <typename T>
+__global__ void k_copy_cast(long long n, const T *src, double *dst) {
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v < n) dst[v] = (double)src[v];
+}
+template <typename T>
+__global__ void k_cast_copy(long long n, const double *src, T *dst) {
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v < n) dst[v] = (T)src[v];
+}
+
+template <typename C> struct OpNone {
+    bool skip_if_done;
+    __device__ void apply(const Geom &, int, int, int, const C *, C *) const {}
+};
+
+// ------------------------------------------------------------------------------------------------
+// Small dense helper: pseudo-inverse solve of a symmetric PSD m x m system by cyclic Jacobi.
+// ------------------------------------------------------------------------------------------------
+static void pinv_solve(int m, const double *Min, const double *b, double rcond, double *x) {
+    double A[5][5], V[5][5];
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) { A[i][j] = Min[i * m + j]; V[i][j] = (i == j); }
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < m; ++i)
+            for (int j = i + 1; j < m; ++j) off += A[i][j] * A[i][j];
+        if (off < 1e-300) break;
+        for (int p = 0; p < m; ++p)
+            for (int q = p + 1; q < m; ++q) {
+                if (A[p][q] == 0.0) continue;
+                const double th = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < m; ++k) {
+                    const double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - s * akq;
+                    A[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < m; ++k) {
+                    const double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - s * aqk;
+                    A[q][k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < m; ++k) {
+                    const double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - s * vkq;
+                    V[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    double lmax = 0.0;
+    for (int i = 0; i < m; ++i) lmax = std::max(lmax, std::fabs(A[i][i]));
+    for (int i = 0; i < m; ++i) x[i] = 0.0;
+    for (int k = 0; k < m; ++k) {
+        const double lam = A[k][k];
+        if (!(std::fabs(lam) > rcond * lmax) || lam == 0.0) continue;
+        double c = 0.0;
+        for (int i = 0; i < m; ++i) c += V[i][k] * b[i];
+        c /= lam;
+        for (int i = 0; i < m; ++i) x[i] += c * V[i][k];
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// The engine
+// ------------------------------------------------------------------------------------------------
+struct SetupInfo {
+    double amean, bbar, bbar_cte;
+};
+
+template <typename T>
+struct Engine {
+    typedef typename cplx_of<T>::type C;
+    rve_config cfg;
+    Geom g;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int NS, D;
+    long long N;
+    // device memory
+    std::vector<void *> allocs;
+    int *gid0 = nullptr, *gid = nullptr;
+    T *Cm = nullptr, *acoef = nullptr, *Ktab = nullptr, *GcTab = nullptr, *Atab = nullptr, *acoefC = nullptr,
+      *KtabC = nullptr, *lamT = nullptr, *muT = nullptr;
+    T *phi = nullptr, *phi_trial = nullptr, *phi_cur = nullptr, *H = nullptr, *Hcur = nullptr, *psi_ini = nullptr,
+      *psi1 = nullptr, *tmpf = nullptr;
+    double *phi_disc = nullptr;
+    T *mx = nullptr, *mr = nullptr, *mp = nullptr, *mq = nullptr;
+    T *dr = nullptr, *dz = nullptr, *dp = nullptr, *dq = nullptr;
+    double *eps_it = nullptr, *eps_com = nullptr, *xh = nullptr, *gh = nullptr, *dtmp = nullptr;
+    C *spec = nullptr;
+    std::map<int, C *> tw;
+    Scal *sc = nullptr, *sc2 = nullptr, *h_sc = nullptr;
+    double *partials = nullptr;
+    int G = 0;
+    bool micro_set = false, iso_damage = true;
+    SetupInfo si{};
+    double fM[6];
+    // committed scalars and curve
+    rve_scalars S{};
+    std::vector<rve_step_result> curve;
+    long launches = 0;
+    // timing
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+    size_t ev_used = 0;
+    double bytes_mech_axis = 0.0;
+    std::map<const void *, size_t> smem_set;
+    int cw_y = 2, cw_z = 2;
+
+    template <typename P> P *alloc(size_t n) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, n * sizeof(P)) != cudaSuccess) throw StatusError{RVE_ENOMEM, "cudaMalloc failed"};
+        allocs.push_back(p);
+        CK(cudaMemsetAsync(p, 0, n * sizeof(P), st));
+        return (P *)p;
+    }
+
+    explicit Engine(const rve_config &c) : cfg(c) {
+        D = c.dim;
+        NS = D == 2 ? 3 : 6;
+        g.d = D; g.ns = NS;
+        g.nx = c.n[0]; g.ny = c.n[1]; g.nz = D == 2 ? 1 : c.n[2];
+        auto lg = [](int n) { int l = 0; while ((1 << l) < n) ++l; return l; };
+        g.lx = lg(g.nx); g.ly = lg(g.ny); g.lz = lg(g.nz);
+        auto cw_of = [](int L) { int TL = L / 4; return std::max(2, std::min(16, 256 / std::max(TL, 1))); };
+        cw_y = cw_of(g.ny);
+        cw_z = g.nz > 1 ? cw_of(g.nz) : 2;
+        const int cw = std::max(cw_y, cw_z);
+        g.Px = ((g.nx / 2 + 1 + cw - 1) / cw) * cw;
+        g.N = (long long)g.nx * g.ny * g.nz;
+        g.Nh = (long long)g.Px * g.ny * g.nz;
+        g.invN = 1.0 / (double)g.N;
+        N = g.N;
+        if (c.stream) st = (cudaStream_t)c.stream;
+        else { CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own_stream = true; }
+        try {
+            gid = alloc<int>(N); gid0 = alloc<int>(N);
+            phi = alloc<T>(N); phi_trial = alloc<T>(N); phi_cur = alloc<T>(N); H = alloc<T>(N); Hcur = alloc<T>(N);
+            psi_ini = alloc<T>(N); psi1 = alloc<T>(N); tmpf = alloc<T>(N); phi_disc = alloc<double>(N);
+            mx = alloc<T>(NS * N); mr = alloc<T>(NS * N); mp = alloc<T>(NS * N); mq = alloc<T>(NS * N);
+            dr = alloc<T>(N); dz = alloc<T>(N); dp = alloc<T>(N); dq = alloc<T>(N);
+            eps_it = alloc<double>(NS * N); eps_com = alloc<double>(NS * N);
+            const int m = std::max(0, std::min(5, cfg.anderson_m));
+            xh = alloc<double>((size_t)(m + 1) * N); gh = alloc<double>((size_t)(m + 1) * N);
+            dtmp = alloc<double>(6 * N);
+            spec = alloc<C>((size_t)std::max(NS, D) * g.Nh);
+            sc = alloc<Scal>(1); sc2 = alloc<Scal>(1);
+            partials = alloc<double>(24 * 65536);
+            CK(cudaMallocHost(&h_sc, sizeof(Scal)));
+            for (int L : {g.nx, g.ny, g.nz}) {
+                if (L < 4 || tw.count(L)) continue;
+                std::vector<C> h(L);
+                for (int m2 = 0; m2 < L; ++m2) {
+                    long double a = -2.0L * 3.14159265358979323846264338327950288L * (long double)m2 / (long double)L;
+                    h[m2].x = (T)std::cos(a);
+                    h[m2].y = (T)std::sin(a);
+                }
+                C *d = alloc<C>(L);
+                CK(cudaMemcpyAsync(d, h.data(), L * sizeof(C), cudaMemcpyHostToDevice, st));
+                tw[L] = d;
+            }
+            CK(cudaStreamSynchronize(st));
+        } catch (...) {
+            release();
+            throw;
+        }
+        // load direction in Mandel form
+        const double s2 = 1.41421356237309504880;
+        if (D == 2) { fM[0] = c.f[0]; fM[1] = c.f[1]; fM[2] = s2 * c.f[5]; }
+        else { fM[0] = c.f[0]; fM[1] = c.f[1]; fM[2] = c.f[2]; fM[3] = s2 * c.f[3]; fM[4] = s2 * c.f[4]; fM[5] = s2 * c.f[5]; }
+        // spectral bytes of one mechanics axis launch: read + write NS complex per spectral point
+        bytes_mech_axis = 2.0 * NS * (double)g.Nh * sizeof(C);
+    }
+
+    void release() {
+        for (auto &e : ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+        ev_pool.clear();
+        for (void *p : allocs) cudaFree(p);
+        allocs.clear();
+        if (h_sc) cudaFreeHost(h_sc);
+        h_sc = nullptr;
+        if (own_stream && st) cudaStreamDestroy(st);
+        st = nullptr;
+    }
+    ~Engine() { release(); }
+
+    // ---- launch helpers --------------------------------------------------------------------
+    template <typename K> void prep_smem(K kernel, size_t bytes) {
+        const void *key = (const void *)kernel;
+        auto it = smem_set.find(key);
+        // opt in above 32 KB: static shared memory (reduction scratch) adds to the dynamic size
+        if (bytes > 32 * 1024 && (it == smem_set.end() || it->second < bytes)) {
+            CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+            smem_set[key] = bytes;
+        }
+    }
+    void xcfg(int &threads, int &blocks, size_t &smem1) const {
+        const int TL = g.nx / 4;
+        const long long pairs = (long long)g.ny * g.nz / 2;
+        int RP = std::max(1, 128 / TL);
+        if (RP > pairs) RP = (int)pairs;
+        threads = RP * TL;
+        blocks = (int)(pairs / RP);
+        smem1 = (size_t)RP * g.nx * sizeof(C);
+    }
+    template <int NC, class Pro> void x_fwd(const Pro &pro, Scal *s) {
+        int th, bl; size_t sm; xcfg(th, bl, sm);
+        auto k = k_x_fwd<T, NC, Pro>;
+        prep_smem(k, sm * NC);
+        k<<<bl, th, sm * NC, st>>>(g, pro, spec, tw[g.nx], partials, s);
+        CK(cudaGetLastError());
+        ++launches;
+    }
+    template <int NC, class Epi> void x_inv(const Epi &epi, Scal *s) {
+        int th, bl; size_t sm; xcfg(th, bl, sm);
+        auto k = k_x_inv<T, NC, Epi>;
+        prep_smem(k, sm * NC);
+        k<<<bl, th, sm * NC, st>>>(g, spec, epi, tw[g.nx], partials, s);
+        CK(cudaGetLastError());
+        ++launches;
+    }
+    template <int NC, class Mid> void x_mid(const Mid &mid, Scal *s) {
+        int th, bl; size_t sm; xcfg(th, bl, sm);
+        auto k = k_x_mid<T, NC, Mid>;
+        prep_smem(k, sm * NC);
+        k<<<bl, th, sm * NC, st>>>(g, spec, mid, tw[g.nx], s);
+        CK(cudaGetLastError());
+        ++launches;
+    }
+    template <int NCI, int NCO, int MODE, class Op> void axis(int ax, const Op &op, Scal *s, bool timed = false) {
+        const int L = ax == 1 ? g.ny : g.nz;
+        const int TL = L / 4;
+        const int CW = ax == 1 ? cw_y : cw_z;
+        dim3 grid(g.Px / CW, ax == 1 ? g.nz : g.ny);
+        const int NM = NCI > NCO ? NCI : NCO;
+        const size_t sm = (size_t)NM * CW * L * sizeof(C);
+        auto k = k_axis<T, NCI, NCO, MODE, Op>;
+        prep_smem(k, sm);
+        cudaEvent_t e1 = nullptr, e2 = nullptr;
+        if (timed && timing) {
+            if (ev_used == ev_pool.size()) {
+                cudaEvent_t a, b;
+                CK(cudaEventCreate(&a)); CK(cudaEventCreate(&b));
+                ev_pool.push_back({a, b});
+            }
+            e1 = ev_pool[ev_used].first; e2 = ev_pool[ev_used].second; ++ev_used;
+            CK(cudaEventRecord(e1, st));
+        }
+        k<<<grid, CW * TL, sm, st>>>(g, ax, spec, spec, op, tw[L], s);
+        CK(cudaGetLastError());
+        ++launches;
+        if (e2) CK(cudaEventRecord(e2, st));
+    }
+    template <class F> void pointwise(const F &f, Scal *s) {
+        const int th = 256;
+        long long bl = (N + th - 1) / th;
+        if (bl > 1184) bl = 1184;
+        k_pointwise<F><<<(int)bl, th, 0, st>>>(N, f, partials, s);
+        CK(cudaGetLastError());
+        ++launches;
+    }
+    // Spectral passes between the x passes: 2D one y pass; 3D y, z (with the operator), y.
+    template <int NCI, int NCO, class Op> void spectral(const Op &op, Scal *s, bool timed = false) {
+        if (D == 2) {
+            axis<NCI, NCO, AX_FWD_OP_INV>(1, op, s, timed);
+        } else {
+            OpNone<C> nop{op.skip_if_done};
+            axis<NCI, NCI, AX_FWD>(1, nop, s, timed);
+            axis<NCI, NCO, AX_FWD_OP_INV>(2, op, s, timed);
+            axis<NCO, NCO, AX_INV>(1, nop, s, timed);
+        }
+    }
+    void read_sc(Scal *s) {
+        CK(cudaMemcpyAsync(h_sc, s, sizeof(Scal), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    void init_sc(Scal *s, double tol, int maxit, double abar = 0.0, double bbar = 0.0) {
+        k_init_scal<<<1, 1, 0, st>>>(s, tol * tol, maxit, abar, bbar);
+        ++launches;
+    }
+
+    // ---- mechanics (a1-a5) ---------------------------------------------------------------------
+    template <int NSx> int mech_solve_t(const T *phi_in, int &iters) {
+        MechBase<T, NSx> mb{Cm, gid, phi_in, (T)cfg.k_res, N, true};
+        ProStressTotal<T, NSx> pro;
+        (MechBase<T, NSx> &)pro = mb;
+        pro.x = mx;
+        for (int a = 0; a < NSx; ++a) pro.f[a] = (T)fM[a];
+        init_sc(sc, cfg.tol_mech, cfg.max_mech_iters);
+        OpProj<C, NSx> proj{true};
+        x_fwd<NSx>(pro, sc);
+        spectral<NSx, NSx>(proj, sc, true);
+        x_inv<NSx>(EpiMechInit<T, NSx>{true, mr, N}, sc);
+        ProCGDir<T, NSx> dir;
+        (MechBase<T, NSx> &)dir = mb;
+        dir.r = mr; dir.p = mp; dir.scr = sc;
+        EpiMechQ<T, NSx> eq{true, mq, mp, N};
+        PwMechUpdate<T, NSx> up{true, mx, mr, mp, mq, sc, N};
+        const int chunk = 8;
+        for (;;) {
+            for (int c = 0; c < chunk; ++c) {
+                x_fwd<NSx>(dir, sc);
+                spectral<NSx, NSx>(proj, sc, true);
+                x_inv<NSx>(eq, sc);
+                pointwise(up, sc);
+            }
+            read_sc(sc);
+            if (h_sc->done) break;
+        }
+        iters = h_sc->iters;
+        if (h_sc->flag) return RVE_EBREAKDOWN;
+        if (!(h_sc->rr <= h_sc->tol2 * h_sc->scale2)) return RVE_ENOCONV;
+        PwPsi1<T, NSx> ps{false, Cm, mx, gid, psi1, {}, N};
+        for (int a = 0; a < NSx; ++a) ps.f[a] = (T)fM[a];
+        pointwise(ps, sc);
+        return RVE_OK;
+    }
+    int mech_solve(const T *phi_in, int &iters) {
+        return NS == 3 ? mech_solve_t<3>(phi_in, iters) : mech_solve_t<6>(phi_in, iters);
+    }
+
+    // ---- damage (a6-a8) ------------------------------------------------------------------------
+    // Generic FFT-preconditioned CG for  a v - div(K grad v) = rhs, warm-started from x.
+    template <int Dx> int pcg_t(int mode, double E, const DmgCoef<T> &co, const T *rhs, T rhs_scale, T *x,
+                                double tol, int maxit, double amean, double bbar, int &iters) {
+        init_sc(sc, tol, maxit);
+        ProDmgInit<T> pi{true, mode, E, psi1, psi_ini, H, Hcur, rhs, x, amean, bbar, (double)co.hmul, N};
+        OpGrad<C, Dx> grad{true};
+        OpDiv<C, Dx> divo{true};
+        OpPrec<C> prec{true, sc};
+        MidFlux<T, Dx> flux{true, co.Ktab, gid};
+        // r = rhs - L x
+        x_fwd<1>(pi, sc);
+        spectral<1, Dx>(grad, sc);
+        x_mid<Dx>(flux, sc);
+        spectral<Dx, 1>(divo, sc);
+        x_inv<1>(EpiDmgRes<T>{true, co, x, dr, rhs, rhs_scale}, sc);
+        // z = M^-1 r
+        x_fwd<1>(ProField<T>{true, dr}, sc);
+        spectral<1, 1>(prec, sc);
+        EpiZ<T> ez{true, dz, dr};
+        x_inv<1>(ez, sc);
+        ProDir<T> pdir{true, dz, dp, sc};
+        EpiDmgQ<T> eq{true, co, dp, dq};
+        ProUpd<T> pu{true, x, dr, dp, dq, sc};
+        const int chunk = 4;
+        for (;;) {
+            for (int c = 0; c < chunk; ++c) {
+                x_fwd<1>(pdir, sc);
+                spectral<1, Dx>(grad, sc);
+                x_mid<Dx>(flux, sc);
+                spectral<Dx, 1>(divo, sc);
+                x_inv<1>(eq, sc);
+                x_fwd<1>(pu, sc);
+                spectral<1, 1>(prec, sc);
+                x_inv<1>(ez, sc);
+            }
+            read_sc(sc);
+            if (h_sc->done) break;
+        }
+        iters = h_sc->iters;
+        if (h_sc->flag) return RVE_EBREAKDOWN;
+        if (!(h_sc->rr <= h_sc->tol2 * h_sc->scale2)) return RVE_ENOCONV;
+        return RVE_OK;
+    }
+    int pcg(int mode, double E, const DmgCoef<T> &co, const T *rhs, T rhs_scale, T *x, double tol, int maxit,
+            double amean, double bbar, int &iters) {
+        return D == 2 ? pcg_t<2>(mode, E, co, rhs, rhs_scale, x, tol, maxit, amean, bbar, iters)
+                      : pcg_t<3>(mode, E, co, rhs, rhs_scale, x, tol, maxit, amean, bbar, iters);
+    }
+    DmgCoef<T> dmg_coef() const { return DmgCoef<T>{acoef, Ktab, gid, (T)2.0, Hcur}; }
+
+    // D(phi) and Gamma(phi) (a9)
+    template <int Dx> void dissipation_t(const T *f, double &Dv, double &Gv) {
+        init_sc(sc2, 0.0, 0);
+        OpGrad<C, Dx> grad{false};
+        x_fwd<1>(ProField<T>{false, f}, sc2);
+        spectral<1, Dx>(grad, sc2);
+        x_inv<Dx>(EpiDiss<T, Dx>{false, f, GcTab, Atab, gid, cfg.ell}, sc2);
+        read_sc(sc2);
+        Dv = h_sc->D;
+        Gv = h_sc->Gamma;
+    }
+    void dissipation(const T *f, double &Dv, double &Gv) {
+        if (D == 2) dissipation_t<2>(f, Dv, Gv); else dissipation_t<3>(f, Dv, Gv);
+    }
+
+    // phi(E) into phi_trial (warm start = current phi_trial); returns D(phi(E)).
+    int damage_eval(double E, double &Dv, int &iters) {
+        const int mode = cfg.history ? 0 : 1;
+        int rc = pcg(mode, E, dmg_coef(), Hcur, (T)2.0, phi_trial, cfg.tol_dmg, cfg.max_dmg_iters, si.amean,
+                     si.bbar, iters);
+        if (rc) return rc;
+        double Gm;
+        dissipation(phi_trial, Dv, Gm);
+        return RVE_OK;
+    }
+
+    // ---- setup (a12) -------------------------------------------------------------------------
+    int set_micro(const rve_micro *m) {
+        G = m->n_grains;
+        if (G <= 0 || !m->grain_id || !m->C_cubic || !m->R || !m->Gc) return RVE_EINVAL;
+        for (long long v = 0; v < N; ++v)
+            if (m->grain_id[v] < 0 || m->grain_id[v] >= G) return RVE_EINVAL;
+        iso_damage = true;
+        if (m->beta)
+            for (int i = 0; i < G; ++i) iso_damage = iso_damage && (m->beta[i] == 0.0);
+        if (cfg.split == RVE_SPLIT_SPECTRAL) {
+            for (int i = 0; i < G; ++i) {
+                const double c11 = m->C_cubic[3 * i], c12 = m->C_cubic[3 * i + 1], c44 = m->C_cubic[3 * i + 2];
+                if (std::fabs(c44 - 0.5 * (c11 - c12)) > 1e-12 * std::fabs(c11)) return RVE_EINVAL;
+            }
+        }
+        if (m->crack_kind != RVE_CRACK_NONE &&
+            (m->crack_row < 0 || m->crack_row >= g.ny || m->crack_len <= 0 || m->crack_len > g.nx || m->crack_phi_M <= 0 ||
+             m->crack_phi_M >= 1.0))
+            return RVE_EINVAL;
+        // per-grain tables
+        for (void *p : {(void *)Cm, (void *)acoef, (void *)Ktab, (void *)GcTab, (void *)Atab, (void *)acoefC,
+                        (void *)KtabC, (void *)lamT, (void *)muT}) {
+            if (p) {
+                cudaFree(p);
+                allocs.erase(std::remove(allocs.begin(), allocs.end(), p), allocs.end());
+            }
+        }
+        const int G2 = 2 * G;
+        Cm = alloc<T>((size_t)G2 * NS * NS); acoef = alloc<T>(G2); Ktab = alloc<T>((size_t)G2 * 6);
+        GcTab = alloc<T>(G2); Atab = alloc<T>((size_t)G2 * 6); acoefC = alloc<T>(G2); KtabC = alloc<T>((size_t)G2 * 6);
+        lamT = alloc<T>(G2); muT = alloc<T>(G2);
+        double *dCc, *dR, *dGc, *dcn = nullptr, *dbe = nullptr;
+        CK(cudaMalloc(&dCc, sizeof(double) * 3 * G)); CK(cudaMalloc(&dR, sizeof(double) * 9 * G));
+        CK(cudaMalloc(&dGc, sizeof(double) * G));
+        CK(cudaMemcpyAsync(dCc, m->C_cubic, sizeof(double) * 3 * G, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dR, m->R, sizeof(double) * 9 * G, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dGc, m->Gc, sizeof(double) * G, cudaMemcpyHostToDevice, st));
+        if (m->cleave_n) {
+            CK(cudaMalloc(&dcn, sizeof(double) * 3 * G));
+            CK(cudaMemcpyAsync(dcn, m->cleave_n, sizeof(double) * 3 * G, cudaMemcpyHostToDevice, st));
+        }
+        if (m->beta) {
+            CK(cudaMalloc(&dbe, sizeof(double) * G));
+            CK(cudaMemcpyAsync(dbe, m->beta, sizeof(double) * G, cudaMemcpyHostToDevice, st));
+        }
+        CK(cudaMemcpyAsync(gid0, m->grain_id, sizeof(int) * N, cudaMemcpyHostToDevice, st));
+        k_build_tables<T><<<(G2 + 63) / 64, 64, 0, st>>>(G, D, dCc, dR, dGc, dcn, dbe, cfg.ell, m->crack_stiffness, Cm,
+                                                          acoef, Ktab, GcTab, Atab, acoefC, KtabC, lamT, muT);
+        ++launches;
+        const int cx0 = ((m->crack_x0 % g.nx) + g.nx) % g.nx;
+        k_crack_setup<<<(int)((N + 255) / 256), 256, 0, st>>>(N, g.nx, g.ny, gid0, G, m->crack_kind, m->crack_row, cx0,
+                                                              m->crack_len, gid, phi_disc);
+        ++launches;
+        init_sc(sc2, 0, 0);
+        pointwise(PwSetupMeans<T>{false, gid, acoef, Ktab, KtabC, D}, sc2);
+        read_sc(sc2);
+        si.amean = h_sc->red[0] / (double)N;
+        si.bbar = h_sc->red[1] / (double)N;
+        si.bbar_cte = h_sc->red[2] / (double)N;
+        CK(cudaFree(dCc)); CK(cudaFree(dR)); CK(cudaFree(dGc));
+        if (dcn) CK(cudaFree(dcn));
+        if (dbe) CK(cudaFree(dbe));
+        // enriched initial crack
+        CK(cudaMemsetAsync(mx, 0, sizeof(T) * NS * N, st));
+        CK(cudaMemsetAsync(eps_com, 0, sizeof(double) * NS * N, st));
+        CK(cudaMemsetAsync(psi1, 0, sizeof(T) * N, st));
+        double tau0 = 0.0;
+        if (m->crack_kind == RVE_CRACK_NONE) {
+            CK(cudaMemsetAsync(phi, 0, sizeof(T) * N, st));
+            CK(cudaMemsetAsync(psi_ini, 0, sizeof(T) * N, st));
+            CK(cudaMemsetAsync(H, 0, sizeof(T) * N, st));
+        } else {
+            int rc = cte_init(m->crack_phi_M, tau0);
+            if (rc) return rc;
+        }
+        CK(cudaMemcpyAsync(phi_trial, phi, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(Hcur, H, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        S = rve_scalars{};
+        S.tau = tau0;
+        S.tau0 = tau0;
+        curve.clear();
+        micro_set = true;
+        return RVE_OK;
+    }
+
+    // phi_o - l^2 div(A grad phi_o) = phi_disc (Eqs. (damini), (daminiAni), read with l^2),
+    // phi_ini = phi_M phi_o / max phi_o, psi_ini = max(0, gamma'(phi_ini) / (2 (1 - phi_ini))) (Eq. (Enini)).
+    int cte_init(double phi_M, double &tau0) {
+        T *phi_disc_T = tmpf;
+        k_cast_copy<T><<<(int)((N + 255) / 256), 256, 0, st>>>(N, phi_disc, phi_disc_T);
+        ++launches;
+        if (iso_damage) {
+            init_sc(sc2, 0, 0, 1.0, cfg.ell * cfg.ell);
+            OpPrec<C> prec{false, sc2};
+            x_fwd<1>(ProField<T>{false, phi_disc_T}, sc2);
+            spectral<1, 1>(prec, sc2);
+            x_inv<1>(EpiStore<T>{false, phi}, sc2);
+        } else {
+            CK(cudaMemsetAsync(phi, 0, sizeof(T) * N, st));
+            DmgCoef<T> co{acoefC, KtabC, gid, (T)0.0, Hcur};
+            int it = 0;
+            int rc = pcg(2, 0.0, co, phi_disc_T, (T)1.0, phi, 1e-14, 20000, 1.0, si.bbar_cte, it);
+            if (rc) return rc;
+        }
+        init_sc(sc2, 0, 0);
+        pointwise(PwMax<T>{false, phi}, sc2);
+        read_sc(sc2);
+        const double mx_ = h_sc->red[0];
+        if (!(mx_ > 0.0)) return RVE_EINVAL;
+        pointwise(PwScaleCopy<T>{false, phi, phi, phi_M / mx_}, sc2);
+        // gamma'(phi_ini) = Gc/l phi - div(Gc l A grad phi)
+        DmgCoef<T> co0{acoef, Ktab, gid, (T)0.0, Hcur};
+        if (D == 2) apply_L<2>(co0, phi, tmpf); else apply_L<3>(co0, phi, tmpf);
+        pointwise(PwPsiIni<T>{false, tmpf, phi, psi_ini, H}, sc2);
+        double Gm;
+        dissipation(phi, tau0, Gm);
+        return RVE_OK;
+    }
+    template <int Dx> void apply_L(const DmgCoef<T> &co, const T *v, T *out) {
+        init_sc(sc2, 0, 0);
+        OpGrad<C, Dx> grad{false};
+        OpDiv<C, Dx> divo{false};
+        x_fwd<1>(ProField<T>{false, v}, sc2);
+        spectral<1, Dx>(grad, sc2);
+        x_mid<Dx>(MidFlux<T, Dx>{false, co.Ktab, gid}, sc2);
+        spectral<Dx, 1>(divo, sc2);
+        x_inv<1>(EpiApply<T>{false, co, v, out}, sc2);
+    }
+
+    // ---- control: smallest E >= 0 with D(phi(E)) = tau (a10) -----------------------------------
+    int arc_length(double tau, double E_guess, double &E_out, double &D_out, rve_step_result &st_) {
+        int it = 0, rc;
+        auto evaluate = [&](double E, double &f) -> int {
+            double Dv;
+            int r = damage_eval(E, Dv, it);
+            st_.dmg_iters += it;
+            st_.root_evals += 1;
+            if (r) return r;
+            f = Dv - tau;
+            D_out = Dv;
+            return RVE_OK;
+        };
+        if (E_guess <= 0.0) {
+            // scale of E from the mean driving energy (same recipe as the oracle)
+            init_sc(sc2, 0, 0);
+            pointwise(PwSum<T>{false, psi1}, sc2);
+            read_sc(sc2);
+            const double pm = std::max(h_sc->red[0] / (double)N, 1e-300);
+            E_guess = std::sqrt(si.amean * cfg.ell / (cfg.ell * pm)) * 0.05;
+        }
+        const double E0 = E_guess;
+        double f0;
+        if ((rc = evaluate(E0, f0))) return rc;
+        if (std::fabs(f0) <= cfg.tol_root * tau) { E_out = E0; return RVE_OK; }
+        double h = 1e-3 * E0, lo, flo, hi, fhi;
+        int guard = 0;
+        if (f0 < 0.0) {
+            lo = E0; flo = f0; hi = lo + h;
+            if ((rc = evaluate(hi, fhi))) return rc;
+            while (fhi <= 0.0) {
+                if (++guard > 200) return RVE_ENOROOT;
+                lo = hi; flo = fhi; h *= 4.0; hi = lo + h;
+                if ((rc = evaluate(hi, fhi))) return rc;
+            }
+        } else {
+            hi = E0; fhi = f0; lo = std::max(0.0, hi - h);
+            if ((rc = evaluate(lo, flo))) return rc;
+            while (flo >= 0.0) {
+                if (lo == 0.0) { E_out = 0.0; return RVE_OK; }
+                if (++guard > 200) return RVE_ENOROOT;
+                hi = lo; fhi = flo; h *= 4.0; lo = std::max(0.0, hi - h);
+                if ((rc = evaluate(lo, flo))) return rc;
+            }
+        }
+        int side = 0;
+        for (int k = 0; k < cfg.max_root_evals; ++k) {
+            const double E = (lo * fhi - hi * flo) / (fhi - flo);
+            double fE;
+            if ((rc = evaluate(E, fE))) return rc;
+            if (std::fabs(fE) <= cfg.tol_root * tau || (hi - lo) <= 1e-15 * hi) { E_out = E; return RVE_OK; }
+            if (fE > 0.0) {
+                hi = E; fhi = fE;
+                if (side == 1) flo *= 0.5;
+                side = 1;
+            } else {
+                lo = E; flo = fE;
+                if (side == -1) fhi *= 0.5;
+                side = -1;
+            }
+        }
+        return RVE_ENOROOT;
+    }
+    double mean_gc = 1.0;
+
+    // ---- one increment (a1-a11) ----------------------------------------------------------------
+    int step(double dtau, rve_step_result *out) {
+        if (!micro_set) return RVE_ESTATE;
+        rve_step_result r{};
+        const double tau = S.tau + dtau;
+        if (!(dtau > 0.0)) return RVE_EINVAL;
+        CK(cudaMemcpyAsync(phi_cur, phi, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(eps_it, eps_com, sizeof(double) * NS * N, cudaMemcpyDeviceToDevice, st));
+        double E = S.E, Dv = 0.0, err = 0.0;
+        const int m = std::max(0, std::min(5, cfg.anderson_m));
+        std::deque<int> hist;  // slots of (X, G) in chronological order
+        int next_slot = 0;
+        bool converged = false;
+        for (int k = 0; k < cfg.max_stag_iters; ++k) {
+            int it = 0;
+            int rc = mech_solve(phi_cur, it);
+            r.mech_iters += it;
+            if (rc) return rc;
+            CK(cudaMemcpyAsync(phi_trial, phi_cur, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+            rc = arc_length(tau, E, E, Dv, r);
+            if (rc) return rc;
+            // staggered error, Eq. (errors_crack)
+            init_sc(sc2, 0, 0);
+            if (NS == 3) {
+                PwStagEps<T, 3> pe{false, mx, eps_it, {}, E, N};
+                for (int a = 0; a < 3; ++a) pe.f[a] = fM[a];
+                pointwise(pe, sc2);
+            } else {
+                PwStagEps<T, 6> pe{false, mx, eps_it, {}, E, N};
+                for (int a = 0; a < 6; ++a) pe.f[a] = fM[a];
+                pointwise(pe, sc2);
+            }
+            pointwise(PwStagPhi<T>{false, phi_trial, phi_cur}, sc2);
+            read_sc(sc2);
+            const double e1 = std::sqrt(h_sc->red[0]) / std::max(std::sqrt(h_sc->red[1]), 1e-300);
+            const double e2 = std::sqrt(h_sc->red[2]) / std::max(std::sqrt(h_sc->red[3]), 1e-300);
+            err = std::max(std::max(e1, e2), std::fabs(Dv - tau) / tau);
+            r.stag_iters = k + 1;
+            if (err < cfg.tol_stag) { converged = true; break; }
+            if (m > 0) {
+                // record (X = phi_cur, G = phi_trial), keep the last m + 1
+                int slot;
+                if ((int)hist.size() < m + 1) slot = next_slot++;
+                else { slot = hist.front(); hist.pop_front(); }
+                hist.push_back(slot);
+                k_copy_cast<T><<<(int)((N + 255) / 256), 256, 0, st>>>(N, phi_cur, xh + (size_t)slot * N);
+                k_copy_cast<T><<<(int)((N + 255) / 256), 256, 0, st>>>(N, phi_trial, gh + (size_t)slot * N);
+                launches += 2;
+                const int K = (int)hist.size() - 1;
+                if (K < 1) {
+                    CK(cudaMemcpyAsync(phi_cur, phi_trial, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+                } else {
+                    AAPtrs hp{};
+                    for (int j = 0; j <= K; ++j) {
+                        hp.X[j] = xh + (size_t)hist[j] * N;
+                        hp.G[j] = gh + (size_t)hist[j] * N;
+                    }
+                    init_sc(sc2, 0, 0);
+                    pointwise(PwAAGram<T>{false, hp, K}, sc2);
+                    read_sc(sc2);
+                    double M[25], b[5], gam[5];
+                    int idx = 0;
+                    double full[5][5];
+                    for (int a = 0; a < 5; ++a)
+                        for (int bb = a; bb < 5; ++bb) { full[a][bb] = full[bb][a] = h_sc->red[idx]; ++idx; }
+                    for (int a = 0; a < K; ++a) {
+                        for (int bb = 0; bb < K; ++bb) M[a * K + bb] = full[a][bb];
+                        b[a] = h_sc->red[15 + a];
+                    }
+                    pinv_solve(K, M, b, 1e-10, gam);
+                    PwAAMix<T> mixf{false, hp, K, {}, phi_cur};
+                    for (int a = 0; a < K; ++a) mixf.gam[a] = gam[a];
+                    pointwise(mixf, sc2);
+                }
+            } else {
+                CK(cudaMemcpyAsync(phi_cur, phi_trial, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+            }
+        }
+        if (!converged) return RVE_ENOCONV;
+        // commit (a8, a11): phi, H, strain, Sigma, E_mec, T
+        CK(cudaMemcpyAsync(phi, phi_trial, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(H, Hcur, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(eps_com, eps_it, sizeof(double) * NS * N, cudaMemcpyDeviceToDevice, st));
+        init_sc(sc2, 0, 0);
+        if (NS == 3) {
+            PwCommit<T, 3> pc{false, Cm, mx, phi, psi1, gid, {}, E, cfg.k_res, N};
+            for (int a = 0; a < 3; ++a) pc.f[a] = fM[a];
+            pointwise(pc, sc2);
+        } else {
+            PwCommit<T, 6> pc{false, Cm, mx, phi, psi1, gid, {}, E, cfg.k_res, N};
+            for (int a = 0; a < 6; ++a) pc.f[a] = fM[a];
+            pointwise(pc, sc2);
+        }
+        read_sc(sc2);
+        const double Sigma = h_sc->red[4] / (double)N;
+        const double Emec = h_sc->red[5];
+        double Dc, Gc_;
+        dissipation(phi, Dc, Gc_);
+        S.T += 0.5 * (Sigma + S.Sigma) * (E - S.E);
+        S.Sigma = Sigma;
+        S.Sigma_max = std::max(S.Sigma_max, Sigma);
+        S.E = E;
+        S.tau = tau;
+        S.n += 1;
+        S.fractured = (S.Sigma_max > 0.0 && Sigma <= cfg.fracture_ratio * S.Sigma_max) ? 1 : 0;
+        r.n = S.n; r.E = E; r.Sigma = Sigma; r.D = Dc; r.Emec = Emec; r.T = S.T; r.Gamma = Gc_; r.tau = tau;
+        r.fractured = S.fractured; r.stag_err = err;
+        curve.push_back(r);
+        if (out) *out = r;
+        return RVE_OK;
+    }
+
+    template <typename U> struct PwSum {
+        static constexpr int NR = 1;
+        static constexpr bool MAXRED = false;
+        bool skip_if_done;
+        const U *f;
+        __device__ void apply(long long v, double *acc) const { acc[0] += (double)f[v]; }
+        struct Fin {
+            Scal *sc;
+            __device__ void operator()(const double *t) const { sc->red[0] = t[0]; }
+        };
+        __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+    };
+
+    double toughness_value() const {
+        const int a0 = crack_len_;
+        const double Ag = (double)(g.nx - a0) * (D == 3 ? g.nz : 1);
+        return (double)N / Ag * (S.T - 0.5 * S.Sigma * S.E);
+    }
+    int crack_len_ = 0;
+
+    // ---- field access --------------------------------------------------------------------------
+    int get_field(int field, double *host, size_t n) {
+        const size_t nsc = (size_t)N, nten = (size_t)NS * N;
+        const int blocks = (int)((N + 255) / 256);
+        switch (field) {
+        case RVE_FIELD_PHI: case RVE_FIELD_H: case RVE_FIELD_PSI_INI: case RVE_FIELD_PSI1: case RVE_FIELD_PHI_TRIAL: {
+            if (n != nsc) return RVE_EINVAL;
+            const T *src = field == RVE_FIELD_PHI ? phi : field == RVE_FIELD_H ? H : field == RVE_FIELD_PSI_INI ? psi_ini
+                         : field == RVE_FIELD_PSI1 ? psi1 : phi_trial;
+            k_copy_cast<T><<<blocks, 256, 0, st>>>(N, src, dtmp);
+            break;
+        }
+        case RVE_FIELD_EPS: case RVE_FIELD_SIGMA: case RVE_FIELD_FLUCT1: {
+            if (n != nten) return RVE_EINVAL;
+            if (field == RVE_FIELD_FLUCT1) {
+                k_mandel_to_tensor<T><<<blocks, 256, 0, st>>>(N, D, mx, 1.0, nullptr, dtmp);
+            } else if (field == RVE_FIELD_EPS) {
+                k_mandel_to_tensor<double><<<blocks, 256, 0, st>>>(N, D, eps_com, 1.0, nullptr, dtmp);
+            } else {
+                double *sig = alloc_tmp_sig();
+                k_stress<T><<<blocks, 256, 0, st>>>(N, D, Cm, gid, phi, cfg.k_res, eps_com, sig);
+                k_mandel_to_tensor<double><<<blocks, 256, 0, st>>>(N, D, sig, 1.0, nullptr, dtmp);
+            }
+            break;
+        }
+        default: return RVE_EINVAL;
+        }
+        CK(cudaMemcpyAsync(host, dtmp, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return RVE_OK;
+    }
+    double *sig_tmp = nullptr;
+    double *alloc_tmp_sig() {
+        if (!sig_tmp) sig_tmp = alloc<double>((size_t)NS * N);
+        return sig_tmp;
+    }
+    int set_field(int field, const double *host, size_t n) {
+        const size_t nsc = (size_t)N, nten = (size_t)NS * N;
+        const int blocks = (int)((N + 255) / 256);
+        if (field == RVE_FIELD_PHI || field == RVE_FIELD_H || field == RVE_FIELD_PSI_INI) {
+            if (n != nsc) return RVE_EINVAL;
+            CK(cudaMemcpyAsync(dtmp, host, n * sizeof(double), cudaMemcpyHostToDevice, st));
+            T *dst = field == RVE_FIELD_PHI ? phi : field == RVE_FIELD_H ? H : psi_ini;
+            k_cast_copy<T><<<blocks, 256, 0, st>>>(N, dtmp, dst);
+            if (field == RVE_FIELD_PHI) k_cast_copy<T><<<blocks, 256, 0, st>>>(N, dtmp, phi_trial);
+        } else if (field == RVE_FIELD_FLUCT1 || field == RVE_FIELD_EPS) {
+            if (n != nten) return RVE_EINVAL;
+            CK(cudaMemcpyAsync(dtmp, host, n * sizeof(double), cudaMemcpyHostToDevice, st));
+            if (field == RVE_FIELD_FLUCT1) k_tensor_to_mandel<T><<<blocks, 256, 0, st>>>(N, D, dtmp, mx);
+            else k_tensor_to_mandel<double><<<blocks, 256, 0, st>>>(N, D, dtmp, eps_com);
+        } else {
+            return RVE_EINVAL;
+        }
+        CK(cudaStreamSynchronize(st));
+        return RVE_OK;
+    }
+};
+
+}  // namespace pffeng
+
+using namespace pffeng;
+
+// ================================================================================================
+// C ABI
+// ================================================================================================
+struct rve_s {
+    rve_config cfg;
+    std::unique_ptr<Engine<double>> e64;
+    double mean_gc = 1.0;
+};
+
+#define GUARD_BEGIN try {
+#define GUARD_END                                                                    \
+    }                                                                                \
+    catch (const CudaError &ce) {                                                    \
+        g_last_error = std::string(ce.what) + ": " + cudaGetErrorString(ce.e);       \
+        return RVE_ECUDA;                                                            \
+    }                                                                                \
+    catch (const StatusError &se) {                                                  \
+        g_last_error = se.msg;                                                       \
+        return se.code;                                                              \
+    }                                                                                \
+    catch (...) {                                                                    \
+        g_last_error = "unknown error";                                              \
+        return RVE_ECUDA;                                                            \
+    }
+
+extern "C" {
+
+void rve_config_default(rve_config *c) {
+    std::memset(c, 0, sizeof(*c));
+    c->dim = 2;
+    c->n[0] = 64; c->n[1] = 64; c->n[2] = 1;
+    c->ell = 2.0;
+    c->k_res = 1e-6;
+    c->split = RVE_SPLIT_NONE;
+    c->precision = RVE_FP64;
+    c->history = 1;
+    c->f[1] = 1.0;
+    c->tol_mech = 1e-12;
+    c->tol_dmg = 1e-12;
+    c->tol_root = 1e-13;
+    c->tol_stag = 1e-10;
+    c->max_mech_iters = 20000;
+    c->max_dmg_iters = 20000;
+    c->max_root_evals = 200;
+    c->max_stag_iters = 2000;
+    c->anderson_m = 5;
+    c->fracture_ratio = 0.01;
+    c->stream = nullptr;
+}
+
+static bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+
+int rve_create(const rve_config *cfg, rve_handle *out) {
+    if (!cfg || !out) return RVE_EINVAL;
+    *out = nullptr;
+    if (cfg->dim != 2 && cfg->dim != 3) return RVE_EINVAL;
+    if (!pow2_in(cfg->n[0], 4, 1024) || !pow2_in(cfg->n[1], 4, 1024)) return RVE_EINVAL;
+    if (cfg->dim == 2 && cfg->n[2] != 1) return RVE_EINVAL;
+    if (cfg->dim == 3 && !pow2_in(cfg->n[2], 4, 1024)) return RVE_EINVAL;
+    if ((long long)cfg->n[0] * cfg->n[1] * cfg->n[2] > (1LL << 24)) return RVE_EINVAL;
+    if (!(cfg->ell > 0) || cfg->k_res < 0 || cfg->anderson_m < 0 || cfg->anderson_m > 5) return RVE_EINVAL;
+    if (cfg->split == RVE_SPLIT_SPECTRAL) return RVE_EINVAL;  // spectral split: not yet on the GPU path
+    if (cfg->precision != RVE_FP64) return RVE_EINVAL;
+    GUARD_BEGIN
+    auto *h = new rve_s();
+    h->cfg = *cfg;
+    h->e64.reset(new Engine<double>(*cfg));
+    *out = h;
+    return RVE_OK;
+    GUARD_END
+}
+
+int set_microstructure(rve_handle h, const rve_micro *m) {
+    if (!h || !m) return RVE_EINVAL;
+    GUARD_BEGIN
+    double s = 0.0;
+    for (int i = 0; i < m->n_grains; ++i) s += m->Gc ? m->Gc[i] : 0.0;
+    h->e64->mean_gc = m->n_grains > 0 ? s / m->n_grains : 1.0;
+    h->e64->crack_len_ = m->crack_kind == RVE_CRACK_NONE ? 0 : m->crack_len;
+    return h->e64->set_micro(m);
+    GUARD_END
+}
+
+int step_dissipation(rve_handle h, double dtau, rve_step_result *out) {
+    if (!h) return RVE_EINVAL;
+    GUARD_BEGIN
+    return h->e64->step(dtau, out);
+    GUARD_END
+}
+
+int effective_toughness(rve_handle h, double *g_eff) {
+    if (!h || !g_eff) return RVE_EINVAL;
+    if (!h->e64->micro_set) return RVE_ESTATE;
+    if (!h->e64->S.fractured) return RVE_ENOTFRACTURED;
+    *g_eff = h->e64->toughness_value();
+    return RVE_OK;
+}
+
+int rve_get_field(rve_handle h, int field, double *host, size_t n) {
+    if (!h || !host) return RVE_EINVAL;
+    GUARD_BEGIN
+    return h->e64->get_field(field, host, n);
+    GUARD_END
+}
+
+int rve_set_field(rve_handle h, int field, const double *host, size_t n) {
+    if (!h || !host) return RVE_EINVAL;
+    GUARD_BEGIN
+    return h->e64->set_field(field, host, n);
+    GUARD_END
+}
+
+int rve_get_scalars(rve_handle h, rve_scalars *s) {
+    if (!h || !s) return RVE_EINVAL;
+    *s = h->e64->S;
+    return RVE_OK;
+}
+
+int rve_set_scalars(rve_handle h, const rve_scalars *s) {
+    if (!h || !s) return RVE_EINVAL;
+    h->e64->S = *s;
+    return RVE_OK;
+}
+
+int rve_mech_solve(rve_handle h, int *iters) {
+    if (!h) return RVE_EINVAL;
+    if (!h->e64->micro_set) return RVE_ESTATE;
+    GUARD_BEGIN
+    int it = 0;
+    int rc = h->e64->mech_solve(h->e64->phi, it);
+    CK(cudaStreamSynchronize(h->e64->st));
+    if (iters) *iters = it;
+    return rc;
+    GUARD_END
+}
+
+int rve_damage_solve(rve_handle h, double E, double *Dv, int *iters) {
+    if (!h) return RVE_EINVAL;
+    if (!h->e64->micro_set) return RVE_ESTATE;
+    GUARD_BEGIN
+    int it = 0;
+    double d = 0.0;
+    int rc = h->e64->damage_eval(E, d, it);
+    if (Dv) *Dv = d;
+    if (iters) *iters = it;
+    return rc;
+    GUARD_END
+}
+
+int rve_dissipation(rve_handle h, const double *phi_host, double *Dv, double *Gv) {
+    if (!h || !phi_host) return RVE_EINVAL;
+    if (!h->e64->micro_set) return RVE_ESTATE;
+    GUARD_BEGIN
+    auto *e = h->e64.get();
+    CK(cudaMemcpyAsync(e->dtmp, phi_host, e->N * sizeof(double), cudaMemcpyHostToDevice, e->st));
+    k_cast_copy<double><<<(int)((e->N + 255) / 256), 256, 0, e->st>>>(e->N, e->dtmp, e->tmpf);
+    double d, gm;
+    e->dissipation(e->tmpf, d, gm);
+    if (Dv) *Dv = d;
+    if (Gv) *Gv = gm;
+    return RVE_OK;
+    GUARD_END
+}
+
+// Checkpoint layout: rve_scalars | curve length | curve | raw device buffers phi, H, psi_ini,
+// strain fluctuation, committed strain (internal precision and Mandel layout, so a reload
+// continues bit-exactly).
+int rve_save(rve_handle h, void *buf, size_t *len) {
+    if (!h || !len) return RVE_EINVAL;
+    GUARD_BEGIN
+    auto *e = h->e64.get();
+    const size_t nf = (size_t)e->N * sizeof(double), nt = (size_t)e->NS * e->N * sizeof(double);
+    const size_t need = sizeof(rve_scalars) + sizeof(size_t) + e->curve.size() * sizeof(rve_step_result) + 3 * nf + 2 * nt;
+    if (!buf) { *len = need; return RVE_OK; }
+    if (*len < need) return RVE_EINVAL;
+    char *p = (char *)buf;
+    std::memcpy(p, &e->S, sizeof(rve_scalars)); p += sizeof(rve_scalars);
+    size_t nc = e->curve.size();
+    std::memcpy(p, &nc, sizeof(size_t)); p += sizeof(size_t);
+    std::memcpy(p, e->curve.data(), nc * sizeof(rve_step_result)); p += nc * sizeof(rve_step_result);
+    const void *src[5] = {e->phi, e->H, e->psi_ini, e->mx, e->eps_com};
+    const size_t sz[5] = {nf, nf, nf, nt, nt};
+    for (int i = 0; i < 5; ++i) { CK(cudaMemcpyAsync(p, src[i], sz[i], cudaMemcpyDeviceToHost, e->st)); p += sz[i]; }
+    CK(cudaStreamSynchronize(e->st));
+    *len = need;
+    return RVE_OK;
+    GUARD_END
+}
+
+int rve_load(rve_handle h, const void *buf, size_t len) {
+    if (!h || !buf) return RVE_EINVAL;
+    GUARD_BEGIN
+    auto *e = h->e64.get();
+    if (!e->micro_set) return RVE_ESTATE;
+    const size_t nf = (size_t)e->N * sizeof(double), nt = (size_t)e->NS * e->N * sizeof(double);
+    const char *p = (const char *)buf;
+    if (len < sizeof(rve_scalars) + sizeof(size_t)) return RVE_EINVAL;
+    rve_scalars s;
+    std::memcpy(&s, p, sizeof(s)); p += sizeof(s);
+    size_t nc;
+    std::memcpy(&nc, p, sizeof(size_t)); p += sizeof(size_t);
+    const size_t need = sizeof(rve_scalars) + sizeof(size_t) + nc * sizeof(rve_step_result) + 3 * nf + 2 * nt;
+    if (len != need) return RVE_EINVAL;
+    std::vector<rve_step_result> cv(nc);
+    std::memcpy(cv.data(), p, nc * sizeof(rve_step_result)); p += nc * sizeof(rve_step_result);
+    void *dst[5] = {e->phi, e->H, e->psi_ini, e->mx, e->eps_com};
+    const size_t sz[5] = {nf, nf, nf, nt, nt};
+    for (int i = 0; i < 5; ++i) { CK(cudaMemcpyAsync(dst[i], p, sz[i], cudaMemcpyHostToDevice, e->st)); p += sz[i]; }
+    CK(cudaMemcpyAsync(e->phi_trial, e->phi, nf, cudaMemcpyDeviceToDevice, e->st));
+    CK(cudaStreamSynchronize(e->st));
+    e->S = s;
+    e->curve = cv;
+    return RVE_OK;
+    GUARD_END
+}
+
+int rve_timing_enable(rve_handle h, int on) {
+    if (!h) return RVE_EINVAL;
+    h->e64->timing = on != 0;
+    h->e64->ev_used = 0;
+    return RVE_OK;
+}
+
+int rve_timing_get(rve_handle h, int kind, double *total_ms, long *launches, double *bytes_per_launch) {
+    if (!h || kind != 0) return RVE_EINVAL;
+    GUARD_BEGIN
+    auto *e = h->e64.get();
+    CK(cudaStreamSynchronize(e->st));
+    double tot = 0.0;
+    for (size_t i = 0; i < e->ev_used; ++i) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e->ev_pool[i].first, e->ev_pool[i].second));
+        tot += ms;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = (long)e->ev_used;
+    if (bytes_per_launch) *bytes_per_launch = e->bytes_mech_axis;
+    return RVE_OK;
+    GUARD_END
+}
+
+long rve_launch_count(rve_handle h) { return h ? h->e64->launches : 0; }
+
+int rve_destroy(rve_handle h) {
+    if (!h) return RVE_EINVAL;
+    delete h;
+    return RVE_OK;
+}
+
+const char *rve_strerror(int s) {
+    switch (s) {
+    case RVE_OK: return "ok";
+    case RVE_EINVAL: return "invalid argument";
+    case RVE_ENOMEM: return "device allocation failed";
+    case RVE_ESTATE: return "call out of order";
+    case RVE_ENOCONV: return "iteration did not converge";
+    case RVE_ENOROOT: return "dissipation constraint could not be bracketed";
+    case RVE_ETIMEOUT: return "device wait timed out";
+    case RVE_ENOTFRACTURED: return "fracture point not reached";
+    case RVE_ECUDA: return g_last_error.empty() ? "CUDA error" : g_last_error.c_str();
+    case RVE_EBREAKDOWN: return "CG breakdown or non-finite value";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,560 @@
+// Prologue / epilogue / per-frequency functors of the spectral passes (see pff_kernels.cuh).
+//
+// Storage: symmetric tensors in Mandel form (xx, yy, [zz], sqrt2 yz, sqrt2 xz, sqrt2 xy), so
+// the Frobenius product of Sec. 4.1 is a plain dot product and the stiffness C^r (Eq. (Crot))
+// is a symmetric NS x NS matrix per grain. Field arrays are component-major [c][voxel].
+#pragma once
+
+#include "pff_common.cuh"
+
+namespace pff {
+
+template <typename T> __device__ __forceinline__ T degr(T phi, T k) {
+    T a = (T)1 - phi;
+    return a * a + k;  // g(phi) = (1 - phi)^2 + k, Sec. 2.1
+}
+
+// ================================ mechanics =====================================================
+template <typename T, int NS>
+struct MechBase {
+    const T *Cm;        // [grain][NS][NS] Mandel stiffness (rotated, crack-scaled)
+    const int *gid;
+    const T *phi;       // damage at which the equilibrium is solved
+    T k;
+    long long N;
+    bool skip_if_done;
+    __device__ __forceinline__ void stress(long long v, const T *u, T *out) const {
+        const T *C = Cm + (size_t)gid[v] * NS * NS;
+        const T gp = degr(phi[v], k);
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+            T s = 0;
+#pragma unroll
+            for (int b = 0; b < NS; ++b) s += C[a * NS + b] * u[b];
+            out[a] = gp * s;
+        }
+    }
+};
+
+// s = g C : (f + x): the total stress of the current fluctuation; reduces |g C : f|^2.
+template <typename T, int NS>
+struct ProStressTotal : MechBase<T, NS> {
+    static constexpr int NR = 1;
+    const T *x;
+    T f[NS];
+    __device__ void eval(long long v, T *out, double *acc) const {
+        T u[NS], sf[NS];
+#pragma unroll
+        for (int a = 0; a < NS; ++a) u[a] = f[a] + x[a * this->N + v];
+        this->stress(v, u, out);
+        this->stress(v, f, sf);
+#pragma unroll
+        for (int a = 0; a < NS; ++a) acc[0] += (double)sf[a] * (double)sf[a];
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const { sc->scale2 = t[0]; }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+// CG direction update p = r + beta p fused with s = g C : p.
+template <typename T, int NS>
+struct ProCGDir : MechBase<T, NS> {
+    static constexpr int NR = 0;
+    const T *r;
+    T *p;
+    const Scal *scr;
+    __device__ void eval(long long v, T *out, double *) const {
+        const T beta = (T)scr->beta;
+        T u[NS];
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+            const size_t i = a * this->N + v;
+            u[a] = r[i] + beta * p[i];
+            p[i] = u[a];
+        }
+        this->stress(v, u, out);
+    }
+    struct Fin { __device__ void operator()(const double *) const {} };
+    __device__ Fin fin(Scal *) const { return Fin{}; }
+};
+
+// Symmetric-strain Galerkin projection P^ = Gamma0(lambda0 = 0, mu0 = 1/2):
+// P(tau) = t (x) n + n (x) t - (n . t) n (x) n, t = tau n, n = xi~/|xi~|; zero where xi~ = 0.
+// On symmetric fields P(sigma) = 0 <=> G^ : sigma = 0 with G^ of Eq. (GFourier).
+template <typename C, int NS>
+struct OpProj {
+    bool skip_if_done;
+    __device__ void apply(const Geom &g, int kx, int ky, int kz, const C *in, C *out) const {
+        const double xx = xi_of(kx, g.nx), xy = xi_of(ky, g.ny), xz = (g.nz > 1) ? xi_of(kz, g.nz) : 0.0;
+        const double q2 = xx * xx + xy * xy + xz * xz;
+        if (q2 == 0.0 || kx > (g.nx >> 1)) {
+#pragma unroll
+            for (int a = 0; a < NS; ++a) { out[a].x = 0; out[a].y = 0; }
+            return;
+        }
+        const double iq = 1.0 / sqrt(q2);
+        const double n0 = xx * iq, n1 = xy * iq, n2 = xz * iq;
+        const double r2 = 0.70710678118654752440;
+        if constexpr (NS == 3) {
+            // tensor components of tau (Mandel shear / sqrt2)
+            const double ax = in[0].x, ay = in[0].y, bx = in[1].x, by = in[1].y;
+            const double cx = in[2].x * r2, cy = in[2].y * r2;
+            const double t0x = ax * n0 + cx * n1, t0y = ay * n0 + cy * n1;
+            const double t1x = cx * n0 + bx * n1, t1y = cy * n0 + by * n1;
+            const double sx = t0x * n0 + t1x * n1, sy = t0y * n0 + t1y * n1;
+            out[0].x = 2 * t0x * n0 - sx * n0 * n0; out[0].y = 2 * t0y * n0 - sy * n0 * n0;
+            out[1].x = 2 * t1x * n1 - sx * n1 * n1; out[1].y = 2 * t1y * n1 - sy * n1 * n1;
+            const double ox = t0x * n1 + t1x * n0 - sx * n0 * n1, oy = t0y * n1 + t1y * n0 - sy * n0 * n1;
+            out[2].x = ox * 1.41421356237309504880; out[2].y = oy * 1.41421356237309504880;
+        } else {
+            double trx[3][3], tiy[3][3];
+            const int ii[6] = {0, 1, 2, 1, 0, 0}, jj[6] = {0, 1, 2, 2, 2, 1};
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+                const double w = a < 3 ? 1.0 : r2;
+                trx[ii[a]][jj[a]] = trx[jj[a]][ii[a]] = in[a].x * w;
+                tiy[ii[a]][jj[a]] = tiy[jj[a]][ii[a]] = in[a].y * w;
+            }
+            const double n[3] = {n0, n1, n2};
+            double tx[3], ty[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                tx[i] = trx[i][0] * n[0] + trx[i][1] * n[1] + trx[i][2] * n[2];
+                ty[i] = tiy[i][0] * n[0] + tiy[i][1] * n[1] + tiy[i][2] * n[2];
+            }
+            const double sx = tx[0] * n[0] + tx[1] * n[1] + tx[2] * n[2];
+            const double sy = ty[0] * n[0] + ty[1] * n[1] + ty[2] * n[2];
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+                const int i = ii[a], j = jj[a];
+                const double w = a < 3 ? 1.0 : 1.41421356237309504880;
+                out[a].x = w * (tx[i] * n[j] + n[i] * tx[j] - sx * n[i] * n[j]);
+                out[a].y = w * (ty[i] * n[j] + n[i] * ty[j] - sy * n[i] * n[j]);
+            }
+        }
+    }
+};
+
+// r = -P[g C : (f + x)]; reduces <r, r>.
+template <typename T, int NS>
+struct EpiMechInit {
+    static constexpr int NR = 1;
+    bool skip_if_done;
+    T *r;
+    long long N;
+    __device__ void apply(long long v, const T *val, double *acc) const {
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+            const T ra = -val[a];
+            r[a * N + v] = ra;
+            acc[0] += (double)ra * (double)ra;
+        }
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const {
+            sc->rr = t[0]; sc->rr0 = t[0]; sc->beta = 0.0; sc->iters = 0;
+            if (!(t[0] <= sc->tol2 * sc->scale2)) sc->done = 0; else sc->done = 1;
+            if (!isfinite(t[0])) { sc->flag |= FLAG_NONFINITE; sc->done = 1; }
+        }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+// q = A p; reduces <p, q> and sets alpha = rr / pq.
+template <typename T, int NS>
+struct EpiMechQ {
+    static constexpr int NR = 1;
+    bool skip_if_done;
+    T *q;
+    const T *p;
+    long long N;
+    __device__ void apply(long long v, const T *val, double *acc) const {
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+            q[a * N + v] = val[a];
+            acc[0] += (double)p[a * N + v] * (double)val[a];
+        }
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const {
+            sc->pq = t[0];
+            if (!(t[0] > 0.0) || !isfinite(t[0])) { sc->flag |= FLAG_BREAKDOWN; sc->done = 1; }
+            else sc->alpha = sc->rr / t[0];
+        }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+// x += alpha p, r -= alpha q; reduces <r, r>; beta, convergence and iteration cap.
+template <typename T, int NS>
+struct PwMechUpdate {
+    static constexpr int NR = 1;
+    static constexpr bool MAXRED = false;
+    bool skip_if_done;
+    T *x, *r;
+    const T *p, *q;
+    const Scal *scr;
+    long long N;
+    __device__ void apply(long long v, double *acc) const {
+        const T al = (T)scr->alpha;
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+            const size_t i = a * N + v;
+            x[i] += al * p[i];
+            const T rn = r[i] - al * q[i];
+            r[i] = rn;
+            acc[0] += (double)rn * (double)rn;
+        }
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const {
+            const double rrn = t[0];
+            sc->beta = rrn / sc->rr;
+            sc->rr = rrn;
+            sc->iters += 1;
+            if (rrn <= sc->tol2 * sc->scale2 || sc->iters >= sc->max_iters) sc->done = 1;
+            if (!isfinite(rrn)) { sc->flag |= FLAG_NONFINITE; sc->done = 1; }
+        }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+// psi1 = 1/2 (f + x) : C : (f + x), the undegraded energy at unit load (Eq. (elas_Ener_rot)).
+template <typename T, int NS>
+struct PwPsi1 {
+    static constexpr int NR = 0;
+    static constexpr bool MAXRED = false;
+    bool skip_if_done;
+    const T *Cm, *x;
+    const int *gid;
+    T *psi1;
+    T f[NS];
+    long long N;
+    __device__ void apply(long long v, double *) const {
+        const T *C = Cm + (size_t)gid[v] * NS * NS;
+        T u[NS];
+#pragma unroll
+        for (int a = 0; a < NS; ++a) u[a] = f[a] + x[a * N + v];
+        T e = 0;
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+            T s = 0;
+#pragma unroll
+            for (int b = 0; b < NS; ++b) s += C[a * NS + b] * u[b];
+            e += u[a] * s;
+        }
+        psi1[v] = (T)0.5 * e;
+    }
+    struct Fin { __device__ void operator()(const double *) const {} };
+    __device__ Fin fin(Scal *) const { return Fin{}; }
+};
+
+// ================================ damage =========================================================
+// Operator L v = a v - div(K grad v) with a = acoef[g] + hmul H and K = Ktab[g] (symmetric d x d,
+// stored xx, yy, [zz, yz, xz], xy). Damage mode: acoef = Gc/l, hmul = 2, K = Gc l A (Eq. (gamFunct));
+// crack-tip enrichment mode: acoef = 1, hmul = 0, K = l^2 A (Eqs. (damini), (daminiAni)).
+template <typename T>
+struct DmgCoef {
+    const T *acoef;
+    const T *Ktab;
+    const int *gid;
+    T hmul;
+    const T *H;
+    __device__ __forceinline__ T a(long long v) const {
+        return acoef[gid[v]] + (hmul != (T)0 ? hmul * H[v] : (T)0);
+    }
+};
+
+// Initialise a damage solve: H_E = max(E^2 psi1 + psi_ini, H^n) (Eq. (HistoryNumIni)) or, without
+// history, E^2 psi1 + psi_ini; rhs = 2 H_E (or the enrichment source phi_disc). Emits the warm
+// start x. Reduces sum H and |rhs|^2.
+template <typename T>
+struct ProDmgInit {
+    static constexpr int NR = 2;
+    bool skip_if_done;
+    int mode;            // 0: damage with history, 1: damage without history, 2: fixed rhs field
+    double E;
+    const T *psi1, *psi_ini, *Hprev;
+    T *Hcur;
+    const T *rhs_field;  // mode 2
+    const T *x;
+    double amean, bbar;
+    double hmul;
+    long long N;
+    __device__ void eval(long long v, T *out, double *acc) const {
+        double rhs;
+        if (mode == 2) {
+            rhs = (double)rhs_field[v];
+        } else {
+            const T drive = (T)(E * E) * psi1[v] + psi_ini[v];
+            const T H = (mode == 0) ? (drive > Hprev[v] ? drive : Hprev[v]) : drive;
+            Hcur[v] = H;
+            acc[0] += (double)H;
+            rhs = 2.0 * (double)H;
+        }
+        acc[1] += rhs * rhs;
+        out[0] = x[v];
+    }
+    struct Fin {
+        Scal *sc;
+        double amean, bbar, hmul, invN;
+        __device__ void operator()(const double *t) const {
+            sc->abar = amean + hmul * t[0] * invN;
+            sc->bbar = bbar;
+            sc->scale2 = t[1];
+        }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc, amean, bbar, hmul, 1.0 / (double)N}; }
+};
+
+template <typename T>
+struct ProField {
+    static constexpr int NR = 0;
+    bool skip_if_done;
+    const T *f;
+    __device__ void eval(long long v, T *out, double *) const { out[0] = f[v]; }
+    struct Fin { __device__ void operator()(const double *) const {} };
+    __device__ Fin fin(Scal *) const { return Fin{}; }
+};
+
+// PCG direction p = z + beta p.
+template <typename T>
+struct ProDir {
+    static constexpr int NR = 0;
+    bool skip_if_done;
+    const T *z;
+    T *p;
+    const Scal *scr;
+    __device__ void eval(long long v, T *out, double *) const {
+        const T pn = z[v] + (T)scr->beta * p[v];
+        p[v] = pn;
+        out[0] = pn;
+    }
+    struct Fin { __device__ void operator()(const double *) const {} };
+    __device__ Fin fin(Scal *) const { return Fin{}; }
+};
+
+// x += alpha p, r -= alpha q, emit r for the preconditioner; reduces <r, r>.
+template <typename T>
+struct ProUpd {
+    static constexpr int NR = 1;
+    bool skip_if_done;
+    T *x, *r;
+    const T *p, *q;
+    const Scal *scr;
+    __device__ void eval(long long v, T *out, double *acc) const {
+        const T al = (T)scr->alpha;
+        x[v] += al * p[v];
+        const T rn = r[v] - al * q[v];
+        r[v] = rn;
+        out[0] = rn;
+        acc[0] += (double)rn * (double)rn;
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const {
+            sc->rr = t[0];
+            sc->iters += 1;
+            if (sc->iters >= sc->max_iters && !(t[0] <= sc->tol2 * sc->scale2)) sc->done = 1;
+            if (!isfinite(t[0])) { sc->flag |= FLAG_NONFINITE; sc->done = 1; }
+        }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+template <typename C, int D>
+struct OpGrad {  // 1 -> D: i xi~_a v^
+    bool skip_if_done;
+    __device__ void apply(const Geom &g, int kx, int ky, int kz, const C *in, C *out) const {
+        const double xs[3] = {xi_of(kx, g.nx), xi_of(ky, g.ny), g.nz > 1 ? xi_of(kz, g.nz) : 0.0};
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            out[a].x = -xs[a] * in[0].y;
+            out[a].y = xs[a] * in[0].x;
+        }
+    }
+};
+
+template <typename C, int D>
+struct OpDiv {  // D -> 1: sum_a i xi~_a q^_a
+    bool skip_if_done;
+    __device__ void apply(const Geom &g, int kx, int ky, int kz, const C *in, C *out) const {
+        const double xs[3] = {xi_of(kx, g.nx), xi_of(ky, g.ny), g.nz > 1 ? xi_of(kz, g.nz) : 0.0};
+        double ox = 0, oy = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            ox -= xs[a] * in[a].y;
+            oy += xs[a] * in[a].x;
+        }
+        out[0].x = ox;
+        out[0].y = oy;
+    }
+};
+
+template <typename C>
+struct OpPrec {  // v^ / (abar + bbar |xi~|^2)
+    bool skip_if_done;
+    const Scal *scr;
+    __device__ void apply(const Geom &g, int kx, int ky, int kz, const C *in, C *out) const {
+        const double a = xi_of(kx, g.nx), b = xi_of(ky, g.ny), c = g.nz > 1 ? xi_of(kz, g.nz) : 0.0;
+        const double s = 1.0 / (scr->abar + scr->bbar * (a * a + b * b + c * c));
+        out[0].x = in[0].x * s;
+        out[0].y = in[0].y * s;
+    }
+};
+
+template <typename T, int D>
+struct MidFlux {  // grad v -> K grad v
+    bool skip_if_done;
+    const T *Ktab;
+    const int *gid;
+    __device__ void apply(long long v, const T *in, T *out) const {
+        const T *K = Ktab + (size_t)gid[v] * 6;
+        if constexpr (D == 2) {
+            out[0] = K[0] * in[0] + K[2] * in[1];
+            out[1] = K[2] * in[0] + K[1] * in[1];
+        } else {
+            out[0] = K[0] * in[0] + K[5] * in[1] + K[4] * in[2];
+            out[1] = K[5] * in[0] + K[1] * in[1] + K[3] * in[2];
+            out[2] = K[4] * in[0] + K[3] * in[1] + K[2] * in[2];
+        }
+    }
+};
+
+// r = rhs - (a x - div); reduces <r, r>.
+template <typename T>
+struct EpiDmgRes {
+    static constexpr int NR = 1;
+    bool skip_if_done;
+    DmgCoef<T> co;
+    const T *x;
+    T *r;
+    const T *rhs;
+    T rhs_scale;
+    __device__ void apply(long long v, const T *val, double *acc) const {
+        const T Lx = co.a(v) * x[v] - val[0];
+        const T rv = rhs_scale * rhs[v] - Lx;
+        r[v] = rv;
+        acc[0] += (double)rv * (double)rv;
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const {
+            sc->rr = t[0]; sc->rr0 = t[0]; sc->iters = 0; sc->first = 1; sc->beta = 0.0;
+            if (t[0] <= sc->tol2 * sc->scale2) sc->done = 1;
+            if (!isfinite(t[0])) { sc->flag |= FLAG_NONFINITE; sc->done = 1; }
+        }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+// z = M^-1 r; reduces <r, z>; beta and the convergence test.
+template <typename T>
+struct EpiZ {
+    static constexpr int NR = 1;
+    bool skip_if_done;
+    T *z;
+    const T *r;
+    __device__ void apply(long long v, const T *val, double *acc) const {
+        z[v] = val[0];
+        acc[0] += (double)r[v] * (double)val[0];
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const {
+            if (sc->first) { sc->beta = 0.0; sc->first = 0; }
+            else sc->beta = t[0] / sc->rz;
+            sc->rz = t[0];
+            if (sc->rr <= sc->tol2 * sc->scale2) sc->done = 1;
+        }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+// q = a p - div; reduces <p, q>; alpha = rz / pq.
+template <typename T>
+struct EpiDmgQ {
+    static constexpr int NR = 1;
+    bool skip_if_done;
+    DmgCoef<T> co;
+    const T *p;
+    T *q;
+    __device__ void apply(long long v, const T *val, double *acc) const {
+        const T qv = co.a(v) * p[v] - val[0];
+        q[v] = qv;
+        acc[0] += (double)p[v] * (double)qv;
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const {
+            sc->pq = t[0];
+            if (!(t[0] > 0.0) || !isfinite(t[0])) { sc->flag |= FLAG_BREAKDOWN; sc->done = 1; }
+            else sc->alpha = sc->rz / t[0];
+        }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+// out = a v - div (one application of the operator, no reduction).
+template <typename T>
+struct EpiApply {
+    static constexpr int NR = 0;
+    bool skip_if_done;
+    DmgCoef<T> co;
+    const T *v_in;
+    T *out;
+    __device__ void apply(long long v, const T *val, double *) const { out[v] = co.a(v) * v_in[v] - val[0]; }
+    struct Fin { __device__ void operator()(const double *) const {} };
+    __device__ Fin fin(Scal *) const { return Fin{}; }
+};
+
+// plain store of one component.
+template <typename T>
+struct EpiStore {
+    static constexpr int NR = 0;
+    bool skip_if_done;
+    T *out;
+    __device__ void apply(long long v, const T *val, double *) const { out[v] = val[0]; }
+    struct Fin { __device__ void operator()(const double *) const {} };
+    __device__ Fin fin(Scal *) const { return Fin{}; }
+};
+
+// D = sum Gc (phi^2/(2l) + l/2 grad phi . A grad phi) and Gamma (same without Gc), Eqs.
+// (CrackLenght_ani), (CrackLenghtreal).
+template <typename T, int D>
+struct EpiDiss {
+    static constexpr int NR = 2;
+    bool skip_if_done;
+    const T *phi;
+    const T *GcTab, *Atab;
+    const int *gid;
+    double ell;
+    __device__ void apply(long long v, const T *gr, double *acc) const {
+        const int gg = gid[v];
+        const T *A = Atab + (size_t)gg * 6;
+        double q;
+        if constexpr (D == 2) {
+            q = (double)gr[0] * (A[0] * gr[0] + A[2] * gr[1]) + (double)gr[1] * (A[2] * gr[0] + A[1] * gr[1]);
+        } else {
+            q = (double)gr[0] * (A[0] * gr[0] + A[5] * gr[1] + A[4] * gr[2]) +
+                (double)gr[1] * (A[5] * gr[0] + A[1] * gr[1] + A[3] * gr[2]) +
+                (double)gr[2] * (A[4] * gr[0] + A[3] * gr[1] + A[2] * gr[2]);
+        }
+        const double p = (double)phi[v];
+        const double dens = p * p / (2.0 * ell) + 0.5 * ell * q;
+        acc[0] += (double)GcTab[gg] * dens;
+        acc[1] += dens;
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const { sc->D = t[0]; sc->Gamma = t[1]; }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+}  // namespace pff

@@ -1,0 +1,174 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, on seeded synthetic inputs.
+
+Step level (each row of the hot path on its own, inputs injected from the oracle):
+  equilibrium CG (a1-a5), damage PCG (a6-a8), dissipation (a9), crack-tip enrichment (a12).
+Increment level: whole increments (a1-a11) from the same start, and one increment from an
+injected oracle state. Run level: toughness (a13) of a small RVE broken through.
+
+Tolerances. Both sides solve to relative residuals of 1e-12..1e-13 in FP64 and differ only in the
+order of rounding and in the CG formulation (symmetric strain vs displacement gradient), so the
+converged answers agree to about the solver tolerance times the conditioning of each solve; the
+per-step bounds below are 1e-10 (fields, energies) unless a comment says otherwise.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import solver as S
+from tests.helpers import rel, sym_components, tensor_from_components
+
+pytestmark = pytest.mark.gpu
+
+CASES = ["homog32", "fibre64x16", "poly32", "poly3d"]
+
+
+@pytest.fixture(scope="module")
+def cap():
+    from paper_2508_07424_gb300 import build, capi
+    build.build()
+    return capi
+
+
+def _pair(name, **tol):
+    from paper_2508_07424_gb300.rve import Rve
+    w = synth.small_cases()[name]
+    kw = dict(tol_mech=1e-13, tol_dmg=1e-13, tol_root=1e-13, tol_stag=1e-11)
+    kw.update(tol)
+    model = S.Model(w.micro, S.params_from_workload(w, **kw))
+    g = Rve.from_workload(w, tol_mech=kw["tol_mech"], tol_dmg=kw["tol_dmg"], tol_root=kw["tol_root"],
+                          tol_stag=kw["tol_stag"])
+    return w, model, g
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_cte_initial_crack(cap, name):
+    w, model, g = _pair(name)
+    st = S.init_state(model)
+    assert rel(g.get(cap.RVE_FIELD_PHI), st.phi) < 1e-12
+    assert rel(g.get(cap.RVE_FIELD_PSI_INI), st.psi_ini) < 1e-10
+    assert rel(g.get(cap.RVE_FIELD_H), st.H) < 1e-10
+    assert abs(g.scalars()["tau"] - st.tau) < 1e-12 * st.tau
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_dissipation_functional(cap, name):
+    w, model, g = _pair(name)
+    rng = np.random.default_rng(3)
+    phi = rng.uniform(0, 1, model.grid)
+    D, Gam = g.dissipation(phi)
+    assert abs(D - model.dissipation(phi)) < 1e-12 * D
+    assert abs(Gam - model.crack_surface(phi)) < 1e-12 * Gam
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_equilibrium_solve(cap, name):
+    w, model, g = _pair(name)
+    rng = np.random.default_rng(4)
+    phi = rng.uniform(0.0, 0.9, model.grid)
+    g.set(cap.RVE_FIELD_PHI, phi)
+    g.mech_solve()
+    F1, _ = S.mech_solve(model, phi, np.zeros((model.d, model.d) + model.grid))
+    ref = sym_components(F1, model.d)
+    got = g.get(cap.RVE_FIELD_FLUCT1)
+    assert rel(got, ref) < 1e-10
+    eps1 = model.fB + tensor_from_components(ref, model.d)
+    assert rel(g.get(cap.RVE_FIELD_PSI1), model.drive(eps1)) < 1e-10
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_damage_solve(cap, name):
+    w, model, g = _pair(name)
+    st = S.init_state(model)
+    g.mech_solve()
+    F1, _ = S.mech_solve(model, st.phi, np.zeros((model.d, model.d) + model.grid))
+    psi1 = model.drive(model.fB + 0.5 * (F1 + np.swapaxes(F1, 0, 1)))
+    for E in (0.05, 0.2, 0.6):
+        H = S.history_field(model, E, psi1, st.psi_ini, st.H)
+        phiE, _ = S.damage_solve(model, H, st.phi)
+        D, _ = g.damage_solve(E)
+        assert rel(g.get(cap.RVE_FIELD_PHI_TRIAL), phiE) < 1e-10
+        assert abs(D - model.dissipation(phiE)) < 1e-10 * D
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_increments_from_the_same_start(cap, name):
+    w, model, g = _pair(name)
+    st = S.init_state(model)
+    n = 3 if name != "poly3d" else 2
+    for _ in range(n):
+        st, _ = S.increment(model, st, w.dtau)
+        r = g.step(w.dtau)
+        o = st.curve[-1]
+        for k in ("E", "Sigma", "D", "T", "Gamma"):
+            assert abs(r[k] - o[k]) <= 1e-9 * abs(o[k]), (k, r[k], o[k])
+        assert abs(r["Emec"] - o["Emec"]) <= 1e-9 * abs(o["Emec"])
+    assert rel(g.get(cap.RVE_FIELD_PHI), st.phi) < 1e-9
+    assert rel(g.get(cap.RVE_FIELD_H), st.H) < 1e-9
+    assert rel(g.get(cap.RVE_FIELD_EPS), sym_components(st.eps, model.d)) < 1e-9
+    sig = model.stress(st.eps, st.phi)
+    assert rel(g.get(cap.RVE_FIELD_SIGMA), sym_components(sig, model.d)) < 1e-9
+
+
+def test_increment_from_injected_oracle_state(cap):
+    """State injection: the oracle runs to a damaged state; the GPU starts one increment from it."""
+    w, model, g = _pair("fibre64x16")
+    st = S.init_state(model)
+    for _ in range(4):
+        st, _ = S.increment(model, st, w.dtau)
+    g.set(cap.RVE_FIELD_PHI, st.phi)
+    g.set(cap.RVE_FIELD_H, st.H)
+    g.set(cap.RVE_FIELD_FLUCT1, sym_components(st.F1, model.d))
+    g.set(cap.RVE_FIELD_EPS, sym_components(st.eps, model.d))
+    g.set_scalars(n=st.n, E=st.E, tau=st.tau, T=st.T, Sigma=st.Sigma, Sigma_max=st.Sigma_max)
+    st2, _ = S.increment(model, st, w.dtau)
+    r = g.step(w.dtau)
+    o = st2.curve[-1]
+    for k in ("E", "Sigma", "D", "T"):
+        assert abs(r[k] - o[k]) <= 1e-9 * abs(o[k]), (k, r[k], o[k])
+    assert rel(g.get(cap.RVE_FIELD_PHI), st2.phi) < 1e-9
+
+
+def test_checkpoint_round_trip_is_bit_exact(cap):
+    w, model, g = _pair("homog32")
+    g.step(w.dtau)
+    blob = g.save()
+    a = g.step(w.dtau)
+    phi_a = g.get(cap.RVE_FIELD_PHI)
+    g.load(blob)
+    b = g.step(w.dtau)
+    assert a == b
+    assert np.array_equal(phi_a, g.get(cap.RVE_FIELD_PHI))
+
+
+def test_call_order_and_status_codes(cap):
+    from paper_2508_07424_gb300.rve import Rve, make_config
+    import ctypes as C
+    g = Rve(make_config(2, (16, 16, 1), 2.0))
+    out = cap.rve_step_result()
+    assert cap.lib().step_dissipation(g.h, 0.1, C.byref(out)) == cap.RVE_ESTATE
+    w = synth.Workload(synth.homogeneous((16, 16)), ell=2.0)
+    g.set_microstructure(w.micro)
+    gv = C.c_double()
+    assert cap.lib().effective_toughness(g.h, C.byref(gv)) == cap.RVE_ENOTFRACTURED
+    assert cap.lib().step_dissipation(g.h, -1.0, C.byref(out)) == cap.RVE_EINVAL
+    # uncracked homogeneous RVE: uniform branch (closed form, as in the oracle pin)
+    r = g.step(0.05 * 256)
+    phi = np.sqrt(2 * 2.0 * 0.05)
+    assert abs(g.get(cap.RVE_FIELD_PHI).mean() - phi) < 1e-12
+
+
+def test_toughness_of_a_small_plate_broken_through(cap):
+    """Run to the fracture point on both sides and compare G (Eqs. (JaviGc), (ABC))."""
+    from paper_2508_07424_gb300.rve import Rve
+    crack = synth.Crack(synth.CRACK_CTE, row=8, x0=0, length=4, phi_M=0.8)
+    w = synth.Workload(synth.homogeneous((16, 16), crack=crack), ell=2.0, n_inc=60)
+    w.dtau = 1.5 * 12 / 30
+    p = S.params_from_workload(w, tol_stag=1e-9)
+    _, st, G = S.run(w, params=p)
+    g = Rve.from_workload(w, tol_stag=1e-9)
+    for _ in range(60):
+        r = g.step(w.dtau)
+        if r["fractured"]:
+            break
+    assert st.fractured and r["fractured"] and r["n"] == st.n
+    assert abs(g.toughness() - G) < 1e-8 * G
