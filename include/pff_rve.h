@@ -177,6 +177,25 @@ long rve_launch_count(rve_handle h);
 int rve_destroy(rve_handle h);
 const char *rve_strerror(int status);
 
+/* Allocation-free D(phi) and Gamma(phi), for callers that cannot allocate device memory when
+ * they need the value (a framework that owns all device memory through its own pool, a
+ * latency-critical loop that must not hit the implicit synchronisation of cudaMalloc/cudaFree,
+ * an embedded caller with a fixed memory budget). The paper has no counterpart: it is a service
+ * entry point of this library, computing the same values as rve_dissipation.
+ *   All pointers are DEVICE pointers owned by the caller: grain_id [n_vox] (x fastest),
+ *   Gc [n_grains], A [n_grains][6] (cleavage tensor of Eq. (PFFani); 3D order xx, yy, zz, yz,
+ *   xz, xy; 2D uses slots 0, 1, 2 for xx, yy, xy), phi [n_vox]; out [2] receives D and Gamma.
+ *   stream: cudaStream_t or NULL. The call is asynchronous on that stream.
+ * Scratch: one fixed 8 MiB __device__ array inside the library, held by every GPU that loads it
+ * until the process exits; nothing is allocated. Grids whose spectra and partial sums do not fit
+ * (e.g. 2D above 512 x 512, 3D above 32^3) return RVE_EINVAL with a message on stderr.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture. All calls share the array: calls that
+ * overlap on the GPU (different streams, different host threads) race and must be ordered by
+ * the caller. Each call clears the parts of the array it relies on. */
+int rve_dissipation_noalloc(int dim, const int n[3], double ell, int n_grains, const int32_t *grain_id,
+                            const double *Gc, const double *A, const double *phi, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,7 +6,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libpff_gb300.so")
-SOURCES = [os.path.join(HERE, "csrc", "pff_engine.cu")]
+SOURCES = [os.path.join(HERE, "csrc", f) for f in ("pff_engine.cu", "pff_noalloc.cu")]
 HEADERS = [os.path.join(HERE, "csrc", f) for f in ("pff_common.cuh", "pff_kernels.cuh", "pff_functors.cuh")] + [
     os.path.join(ROOT, "include", "pff_rve.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

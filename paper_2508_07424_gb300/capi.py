@@ -65,6 +65,8 @@ _SIGS = {
     "rve_launch_count": (C.c_long, [rve_handle]),
     "rve_destroy": (C.c_int, [rve_handle]),
     "rve_strerror": (C.c_char_p, [C.c_int]),
+    "rve_dissipation_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_double, C.c_int, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 EXPORTED = tuple(_SIGS)
