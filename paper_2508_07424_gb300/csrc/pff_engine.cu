@@ -459,15 +459,43 @@ struct SetupInfo {
     double amean, bbar, bbar_cte;
 };
 
-template <typename T>
-struct Engine {
-    typedef typename cplx_of<T>::type C;
+// Precision-independent part of a handle: configuration, committed scalars, load curve.
+struct EngineBase {
     rve_config cfg;
     Geom g;
     cudaStream_t st = nullptr;
     bool own_stream = false;
-    int NS, D;
-    long long N;
+    int NS = 3, D = 2;
+    long long N = 0;
+    bool micro_set = false;
+    rve_scalars S{};
+    std::vector<rve_step_result> curve;
+    long launches = 0;
+    int crack_len_ = 0;
+    bool timing = false;
+    virtual ~EngineBase() {}
+    virtual int set_micro(const rve_micro *m) = 0;
+    virtual int step(double dtau, rve_step_result *out) = 0;
+    virtual int get_field(int field, double *host, size_t n) = 0;
+    virtual int set_field(int field, const double *host, size_t n) = 0;
+    virtual int mech_solve_committed(int &iters) = 0;
+    virtual int damage_eval_api(double E, double &Dv, int &iters) = 0;
+    virtual int dissipation_host(const double *phi_host, double &Dv, double &Gv) = 0;
+    virtual size_t state_bytes() const = 0;
+    virtual void save_state(char *p) = 0;
+    virtual void load_state(const char *p) = 0;
+    virtual void timing_reset() = 0;
+    virtual void timing_get(double &ms, long &n, double &bytes) = 0;
+    double toughness_value() const {
+        const double Ag = (double)(g.nx - crack_len_) * (D == 3 ? g.nz : 1);
+        return (double)N / Ag * (S.T - 0.5 * S.Sigma * S.E);
+    }
+};
+
+template <typename T>
+struct Engine : EngineBase {
+    typedef typename cplx_of<T>::type C;
+    static constexpr bool kSingle = sizeof(T) == 4;
     // device memory
     std::vector<void *> allocs;
     int *gid0 = nullptr, *gid = nullptr;
@@ -484,15 +512,11 @@ struct Engine {
     Scal *sc = nullptr, *sc2 = nullptr, *h_sc = nullptr;
     double *partials = nullptr;
     int G = 0;
-    bool micro_set = false, iso_damage = true;
+    bool iso_damage = true;
     SetupInfo si{};
     double fM[6];
-    // committed scalars and curve
-    rve_scalars S{};
-    std::vector<rve_step_result> curve;
-    long launches = 0;
+    T *xi_x = nullptr, *xi_y = nullptr, *xi_z = nullptr;
     // timing
-    bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
     size_t ev_used = 0;
     double bytes_mech_axis = 0.0;
@@ -507,7 +531,16 @@ struct Engine {
         return (P *)p;
     }
 
-    explicit Engine(const rve_config &c) : cfg(c) {
+    explicit Engine(const rve_config &c) {
+        cfg = c;
+        if (kSingle) {
+            // FP32 field arithmetic: tolerances below what single-precision operators resolve
+            // are raised (the refinement loops then converge on the true residual).
+            cfg.tol_mech = std::max(cfg.tol_mech, 1e-6);
+            cfg.tol_dmg = std::max(cfg.tol_dmg, 1e-6);
+            cfg.tol_root = std::max(cfg.tol_root, 1e-6);
+            cfg.tol_stag = std::max(cfg.tol_stag, 1e-5);
+        }
         D = c.dim;
         NS = D == 2 ? 3 : 6;
         g.d = D; g.ns = NS;
@@ -551,6 +584,25 @@ struct Engine {
                 CK(cudaMemcpyAsync(d, h.data(), L * sizeof(C), cudaMemcpyHostToDevice, st));
                 tw[L] = d;
             }
+            // frequency tables xi~ = 2 pi k / n with the Nyquist frequency set to zero
+            auto xi_host = [](int n, int len, bool half) {
+                std::vector<T> v(len, (T)0);
+                const int lim = half ? n / 2 + 1 : n;
+                for (int k = 0; k < lim && k < len; ++k) {
+                    const int kk = k <= n / 2 ? k : k - n;
+                    v[k] = (2 * k == n) ? (T)0
+                                        : (T)(2.0L * 3.14159265358979323846264338327950288L * (long double)kk / (long double)n);
+                }
+                return v;
+            };
+            auto up = [&](const std::vector<T> &h) {
+                T *d = alloc<T>(h.size());
+                CK(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+                return d;
+            };
+            xi_x = up(xi_host(g.nx, g.Px, true));
+            xi_y = up(xi_host(g.ny, g.ny, false));
+            xi_z = up(xi_host(g.nz, g.nz, false));
             CK(cudaStreamSynchronize(st));
         } catch (...) {
             release();
@@ -575,6 +627,7 @@ struct Engine {
         st = nullptr;
     }
     ~Engine() { release(); }
+    XiTab<T> xitab() const { return XiTab<T>{xi_x, xi_y, xi_z}; }
 
     // ---- launch helpers --------------------------------------------------------------------
     template <typename K> void prep_smem(K kernel, size_t bytes) {
@@ -679,7 +732,7 @@ struct Engine {
         pro.x = mx;
         for (int a = 0; a < NSx; ++a) pro.f[a] = (T)fM[a];
         init_sc(sc, cfg.tol_mech, cfg.max_mech_iters);
-        OpProj<C, NSx> proj{true};
+        OpProj<C, NSx> proj{true, xitab()};
         x_fwd<NSx>(pro, sc);
         spectral<NSx, NSx>(proj, sc, true);
         x_inv<NSx>(EpiMechInit<T, NSx>{true, mr, N}, sc);
@@ -688,20 +741,34 @@ struct Engine {
         dir.r = mr; dir.p = mp; dir.scr = sc;
         EpiMechQ<T, NSx> eq{true, mq, mp, N};
         PwMechUpdate<T, NSx> up{true, mx, mr, mp, mq, sc, N};
+        // FP64: one CG pass (as the oracle). FP32: iterative refinement -- each pass restarts CG
+        // from the equilibrium residual recomputed from the current strain, until that true
+        // residual meets the tolerance (a pass that needs no iteration).
+        const int passes = kSingle ? 8 : 1;
         const int chunk = 8;
-        for (;;) {
-            for (int c = 0; c < chunk; ++c) {
-                x_fwd<NSx>(dir, sc);
+        iters = 0;
+        for (int pass = 0; pass < passes; ++pass) {
+            if (pass > 0) {
+                init_sc(sc, cfg.tol_mech, std::max(1, cfg.max_mech_iters - iters));
+                x_fwd<NSx>(pro, sc);
                 spectral<NSx, NSx>(proj, sc, true);
-                x_inv<NSx>(eq, sc);
-                pointwise(up, sc);
+                x_inv<NSx>(EpiMechInit<T, NSx>{true, mr, N}, sc);
             }
-            read_sc(sc);
-            if (h_sc->done) break;
+            for (;;) {
+                for (int c = 0; c < chunk; ++c) {
+                    x_fwd<NSx>(dir, sc);
+                    spectral<NSx, NSx>(proj, sc, true);
+                    x_inv<NSx>(eq, sc);
+                    pointwise(up, sc);
+                }
+                read_sc(sc);
+                if (h_sc->done) break;
+            }
+            iters += h_sc->iters;
+            if (h_sc->flag) return RVE_EBREAKDOWN;
+            if (!(h_sc->rr <= h_sc->tol2 * h_sc->scale2)) return RVE_ENOCONV;
+            if (!kSingle || h_sc->iters == 0) break;
         }
-        iters = h_sc->iters;
-        if (h_sc->flag) return RVE_EBREAKDOWN;
-        if (!(h_sc->rr <= h_sc->tol2 * h_sc->scale2)) return RVE_ENOCONV;
         PwPsi1<T, NSx> ps{false, Cm, mx, gid, psi1, {}, N};
         for (int a = 0; a < NSx; ++a) ps.f[a] = (T)fM[a];
         pointwise(ps, sc);
@@ -715,44 +782,50 @@ struct Engine {
     // Generic FFT-preconditioned CG for  a v - div(K grad v) = rhs, warm-started from x.
     template <int Dx> int pcg_t(int mode, double E, const DmgCoef<T> &co, const T *rhs, T rhs_scale, T *x,
                                 double tol, int maxit, double amean, double bbar, int &iters) {
-        init_sc(sc, tol, maxit);
         ProDmgInit<T> pi{true, mode, E, psi1, psi_ini, H, Hcur, rhs, x, amean, bbar, (double)co.hmul, N};
-        OpGrad<C, Dx> grad{true};
-        OpDiv<C, Dx> divo{true};
-        OpPrec<C> prec{true, sc};
+        OpGrad<C, Dx> grad{true, xitab()};
+        OpDiv<C, Dx> divo{true, xitab()};
+        OpPrec<C> prec{true, sc, xitab()};
         MidFlux<T, Dx> flux{true, co.Ktab, gid};
-        // r = rhs - L x
-        x_fwd<1>(pi, sc);
-        spectral<1, Dx>(grad, sc);
-        x_mid<Dx>(flux, sc);
-        spectral<Dx, 1>(divo, sc);
-        x_inv<1>(EpiDmgRes<T>{true, co, x, dr, rhs, rhs_scale}, sc);
-        // z = M^-1 r
-        x_fwd<1>(ProField<T>{true, dr}, sc);
-        spectral<1, 1>(prec, sc);
         EpiZ<T> ez{true, dz, dr};
-        x_inv<1>(ez, sc);
         ProDir<T> pdir{true, dz, dp, sc};
         EpiDmgQ<T> eq{true, co, dp, dq};
         ProUpd<T> pu{true, x, dr, dp, dq, sc};
+        // FP64: one PCG pass; FP32: passes restarted from the true residual (see mech_solve_t).
+        const int passes = kSingle ? 8 : 1;
         const int chunk = 4;
-        for (;;) {
-            for (int c = 0; c < chunk; ++c) {
-                x_fwd<1>(pdir, sc);
-                spectral<1, Dx>(grad, sc);
-                x_mid<Dx>(flux, sc);
-                spectral<Dx, 1>(divo, sc);
-                x_inv<1>(eq, sc);
-                x_fwd<1>(pu, sc);
-                spectral<1, 1>(prec, sc);
-                x_inv<1>(ez, sc);
+        iters = 0;
+        for (int pass = 0; pass < passes; ++pass) {
+            init_sc(sc, tol, std::max(1, maxit - iters));
+            // r = rhs - L x
+            x_fwd<1>(pi, sc);
+            spectral<1, Dx>(grad, sc);
+            x_mid<Dx>(flux, sc);
+            spectral<Dx, 1>(divo, sc);
+            x_inv<1>(EpiDmgRes<T>{true, co, x, dr, rhs, rhs_scale}, sc);
+            // z = M^-1 r
+            x_fwd<1>(ProField<T>{true, dr}, sc);
+            spectral<1, 1>(prec, sc);
+            x_inv<1>(ez, sc);
+            for (;;) {
+                for (int c = 0; c < chunk; ++c) {
+                    x_fwd<1>(pdir, sc);
+                    spectral<1, Dx>(grad, sc);
+                    x_mid<Dx>(flux, sc);
+                    spectral<Dx, 1>(divo, sc);
+                    x_inv<1>(eq, sc);
+                    x_fwd<1>(pu, sc);
+                    spectral<1, 1>(prec, sc);
+                    x_inv<1>(ez, sc);
+                }
+                read_sc(sc);
+                if (h_sc->done) break;
             }
-            read_sc(sc);
-            if (h_sc->done) break;
+            iters += h_sc->iters;
+            if (h_sc->flag) return RVE_EBREAKDOWN;
+            if (!(h_sc->rr <= h_sc->tol2 * h_sc->scale2)) return RVE_ENOCONV;
+            if (!kSingle || h_sc->iters == 0) break;
         }
-        iters = h_sc->iters;
-        if (h_sc->flag) return RVE_EBREAKDOWN;
-        if (!(h_sc->rr <= h_sc->tol2 * h_sc->scale2)) return RVE_ENOCONV;
         return RVE_OK;
     }
     int pcg(int mode, double E, const DmgCoef<T> &co, const T *rhs, T rhs_scale, T *x, double tol, int maxit,
@@ -765,7 +838,7 @@ struct Engine {
     // D(phi) and Gamma(phi) (a9)
     template <int Dx> void dissipation_t(const T *f, double &Dv, double &Gv) {
         init_sc(sc2, 0.0, 0);
-        OpGrad<C, Dx> grad{false};
+        OpGrad<C, Dx> grad{false, xitab()};
         x_fwd<1>(ProField<T>{false, f}, sc2);
         spectral<1, Dx>(grad, sc2);
         x_inv<Dx>(EpiDiss<T, Dx>{false, f, GcTab, Atab, gid, cfg.ell}, sc2);
@@ -789,7 +862,7 @@ struct Engine {
     }
 
     // ---- setup (a12) -------------------------------------------------------------------------
-    int set_micro(const rve_micro *m) {
+    int set_micro(const rve_micro *m) override {
         G = m->n_grains;
         if (G <= 0 || !m->grain_id || !m->C_cubic || !m->R || !m->Gc) return RVE_EINVAL;
         for (long long v = 0; v < N; ++v)
@@ -882,7 +955,7 @@ struct Engine {
         ++launches;
         if (iso_damage) {
             init_sc(sc2, 0, 0, 1.0, cfg.ell * cfg.ell);
-            OpPrec<C> prec{false, sc2};
+            OpPrec<C> prec{false, sc2, xitab()};
             x_fwd<1>(ProField<T>{false, phi_disc_T}, sc2);
             spectral<1, 1>(prec, sc2);
             x_inv<1>(EpiStore<T>{false, phi}, sc2);
@@ -890,7 +963,7 @@ struct Engine {
             CK(cudaMemsetAsync(phi, 0, sizeof(T) * N, st));
             DmgCoef<T> co{acoefC, KtabC, gid, (T)0.0, Hcur};
             int it = 0;
-            int rc = pcg(2, 0.0, co, phi_disc_T, (T)1.0, phi, 1e-14, 20000, 1.0, si.bbar_cte, it);
+            int rc = pcg(2, 0.0, co, phi_disc_T, (T)1.0, phi, kSingle ? 1e-6 : 1e-14, 20000, 1.0, si.bbar_cte, it);
             if (rc) return rc;
         }
         init_sc(sc2, 0, 0);
@@ -909,8 +982,8 @@ struct Engine {
     }
     template <int Dx> void apply_L(const DmgCoef<T> &co, const T *v, T *out) {
         init_sc(sc2, 0, 0);
-        OpGrad<C, Dx> grad{false};
-        OpDiv<C, Dx> divo{false};
+        OpGrad<C, Dx> grad{false, xitab()};
+        OpDiv<C, Dx> divo{false, xitab()};
         x_fwd<1>(ProField<T>{false, v}, sc2);
         spectral<1, Dx>(grad, sc2);
         x_mid<Dx>(MidFlux<T, Dx>{false, co.Ktab, gid}, sc2);
@@ -981,10 +1054,8 @@ struct Engine {
         }
         return RVE_ENOROOT;
     }
-    double mean_gc = 1.0;
-
     // ---- one increment (a1-a11) ----------------------------------------------------------------
-    int step(double dtau, rve_step_result *out) {
+    int step(double dtau, rve_step_result *out) override {
         if (!micro_set) return RVE_ESTATE;
         rve_step_result r{};
         const double tau = S.tau + dtau;
@@ -1108,15 +1179,52 @@ struct Engine {
         __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
     };
 
-    double toughness_value() const {
-        const int a0 = crack_len_;
-        const double Ag = (double)(g.nx - a0) * (D == 3 ? g.nz : 1);
-        return (double)N / Ag * (S.T - 0.5 * S.Sigma * S.E);
+
+    // ---- services of the C ABI ------------------------------------------------------------------
+    int mech_solve_committed(int &iters) override {
+        int rc = mech_solve(phi, iters);
+        CK(cudaStreamSynchronize(st));
+        return rc;
     }
-    int crack_len_ = 0;
+    int damage_eval_api(double E, double &Dv, int &iters) override { return damage_eval(E, Dv, iters); }
+    int dissipation_host(const double *phi_host, double &Dv, double &Gv) override {
+        CK(cudaMemcpyAsync(dtmp, phi_host, N * sizeof(double), cudaMemcpyHostToDevice, st));
+        k_cast_copy<T><<<(int)((N + 255) / 256), 256, 0, st>>>(N, dtmp, tmpf);
+        ++launches;
+        dissipation(tmpf, Dv, Gv);
+        return RVE_OK;
+    }
+    // checkpoint payload: phi, H, psi_ini, strain fluctuation (field precision), committed strain (FP64)
+    size_t state_bytes() const override { return (size_t)N * sizeof(T) * (3 + NS) + (size_t)NS * N * sizeof(double); }
+    void save_state(char *p) override {
+        const void *src[5] = {phi, H, psi_ini, mx, eps_com};
+        const size_t sz[5] = {N * sizeof(T), N * sizeof(T), N * sizeof(T), NS * N * sizeof(T), NS * N * sizeof(double)};
+        for (int i = 0; i < 5; ++i) { CK(cudaMemcpyAsync(p, src[i], sz[i], cudaMemcpyDeviceToHost, st)); p += sz[i]; }
+        CK(cudaStreamSynchronize(st));
+    }
+    void load_state(const char *p) override {
+        void *dst[5] = {phi, H, psi_ini, mx, eps_com};
+        const size_t sz[5] = {N * sizeof(T), N * sizeof(T), N * sizeof(T), NS * N * sizeof(T), NS * N * sizeof(double)};
+        for (int i = 0; i < 5; ++i) { CK(cudaMemcpyAsync(dst[i], p, sz[i], cudaMemcpyHostToDevice, st)); p += sz[i]; }
+        CK(cudaMemcpyAsync(phi_trial, phi, N * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    void timing_reset() override { ev_used = 0; }
+    void timing_get(double &ms, long &n, double &bytes) override {
+        CK(cudaStreamSynchronize(st));
+        double tot = 0.0;
+        for (size_t i = 0; i < ev_used; ++i) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, ev_pool[i].first, ev_pool[i].second));
+            tot += t;
+        }
+        ms = tot;
+        n = (long)ev_used;
+        bytes = bytes_mech_axis;
+    }
 
     // ---- field access --------------------------------------------------------------------------
-    int get_field(int field, double *host, size_t n) {
+    int get_field(int field, double *host, size_t n) override {
         const size_t nsc = (size_t)N, nten = (size_t)NS * N;
         const int blocks = (int)((N + 255) / 256);
         switch (field) {
@@ -1151,7 +1259,7 @@ struct Engine {
         if (!sig_tmp) sig_tmp = alloc<double>((size_t)NS * N);
         return sig_tmp;
     }
-    int set_field(int field, const double *host, size_t n) {
+    int set_field(int field, const double *host, size_t n) override {
         const size_t nsc = (size_t)N, nten = (size_t)NS * N;
         const int blocks = (int)((N + 255) / 256);
         if (field == RVE_FIELD_PHI || field == RVE_FIELD_H || field == RVE_FIELD_PSI_INI) {
@@ -1182,8 +1290,7 @@ using namespace pffeng;
 // ================================================================================================
 struct rve_s {
     rve_config cfg;
-    std::unique_ptr<Engine<double>> e64;
-    double mean_gc = 1.0;
+    std::unique_ptr<EngineBase> e;
 };
 
 #define GUARD_BEGIN try {
@@ -1239,11 +1346,17 @@ int rve_create(const rve_config *cfg, rve_handle *out) {
     if ((long long)cfg->n[0] * cfg->n[1] * cfg->n[2] > (1LL << 24)) return RVE_EINVAL;
     if (!(cfg->ell > 0) || cfg->k_res < 0 || cfg->anderson_m < 0 || cfg->anderson_m > 5) return RVE_EINVAL;
     if (cfg->split == RVE_SPLIT_SPECTRAL) return RVE_EINVAL;  // spectral split: not yet on the GPU path
-    if (cfg->precision != RVE_FP64) return RVE_EINVAL;
+    if (cfg->precision != RVE_FP64 && cfg->precision != RVE_FP32R) return RVE_EINVAL;
     GUARD_BEGIN
     auto *h = new rve_s();
     h->cfg = *cfg;
-    h->e64.reset(new Engine<double>(*cfg));
+    try {
+        if (cfg->precision == RVE_FP64) h->e.reset(new Engine<double>(*cfg));
+        else h->e.reset(new Engine<float>(*cfg));
+    } catch (...) {
+        delete h;
+        throw;
+    }
     *out = h;
     return RVE_OK;
     GUARD_END
@@ -1252,62 +1365,58 @@ int rve_create(const rve_config *cfg, rve_handle *out) {
 int set_microstructure(rve_handle h, const rve_micro *m) {
     if (!h || !m) return RVE_EINVAL;
     GUARD_BEGIN
-    double s = 0.0;
-    for (int i = 0; i < m->n_grains; ++i) s += m->Gc ? m->Gc[i] : 0.0;
-    h->e64->mean_gc = m->n_grains > 0 ? s / m->n_grains : 1.0;
-    h->e64->crack_len_ = m->crack_kind == RVE_CRACK_NONE ? 0 : m->crack_len;
-    return h->e64->set_micro(m);
+    h->e->crack_len_ = m->crack_kind == RVE_CRACK_NONE ? 0 : m->crack_len;
+    return h->e->set_micro(m);
     GUARD_END
 }
 
 int step_dissipation(rve_handle h, double dtau, rve_step_result *out) {
     if (!h) return RVE_EINVAL;
     GUARD_BEGIN
-    return h->e64->step(dtau, out);
+    return h->e->step(dtau, out);
     GUARD_END
 }
 
 int effective_toughness(rve_handle h, double *g_eff) {
     if (!h || !g_eff) return RVE_EINVAL;
-    if (!h->e64->micro_set) return RVE_ESTATE;
-    if (!h->e64->S.fractured) return RVE_ENOTFRACTURED;
-    *g_eff = h->e64->toughness_value();
+    if (!h->e->micro_set) return RVE_ESTATE;
+    if (!h->e->S.fractured) return RVE_ENOTFRACTURED;
+    *g_eff = h->e->toughness_value();
     return RVE_OK;
 }
 
 int rve_get_field(rve_handle h, int field, double *host, size_t n) {
     if (!h || !host) return RVE_EINVAL;
     GUARD_BEGIN
-    return h->e64->get_field(field, host, n);
+    return h->e->get_field(field, host, n);
     GUARD_END
 }
 
 int rve_set_field(rve_handle h, int field, const double *host, size_t n) {
     if (!h || !host) return RVE_EINVAL;
     GUARD_BEGIN
-    return h->e64->set_field(field, host, n);
+    return h->e->set_field(field, host, n);
     GUARD_END
 }
 
 int rve_get_scalars(rve_handle h, rve_scalars *s) {
     if (!h || !s) return RVE_EINVAL;
-    *s = h->e64->S;
+    *s = h->e->S;
     return RVE_OK;
 }
 
 int rve_set_scalars(rve_handle h, const rve_scalars *s) {
     if (!h || !s) return RVE_EINVAL;
-    h->e64->S = *s;
+    h->e->S = *s;
     return RVE_OK;
 }
 
 int rve_mech_solve(rve_handle h, int *iters) {
     if (!h) return RVE_EINVAL;
-    if (!h->e64->micro_set) return RVE_ESTATE;
+    if (!h->e->micro_set) return RVE_ESTATE;
     GUARD_BEGIN
     int it = 0;
-    int rc = h->e64->mech_solve(h->e64->phi, it);
-    CK(cudaStreamSynchronize(h->e64->st));
+    int rc = h->e->mech_solve_committed(it);
     if (iters) *iters = it;
     return rc;
     GUARD_END
@@ -1315,11 +1424,11 @@ int rve_mech_solve(rve_handle h, int *iters) {
 
 int rve_damage_solve(rve_handle h, double E, double *Dv, int *iters) {
     if (!h) return RVE_EINVAL;
-    if (!h->e64->micro_set) return RVE_ESTATE;
+    if (!h->e->micro_set) return RVE_ESTATE;
     GUARD_BEGIN
     int it = 0;
     double d = 0.0;
-    int rc = h->e64->damage_eval(E, d, it);
+    int rc = h->e->damage_eval_api(E, d, it);
     if (Dv) *Dv = d;
     if (iters) *iters = it;
     return rc;
@@ -1328,28 +1437,24 @@ int rve_damage_solve(rve_handle h, double E, double *Dv, int *iters) {
 
 int rve_dissipation(rve_handle h, const double *phi_host, double *Dv, double *Gv) {
     if (!h || !phi_host) return RVE_EINVAL;
-    if (!h->e64->micro_set) return RVE_ESTATE;
+    if (!h->e->micro_set) return RVE_ESTATE;
     GUARD_BEGIN
-    auto *e = h->e64.get();
-    CK(cudaMemcpyAsync(e->dtmp, phi_host, e->N * sizeof(double), cudaMemcpyHostToDevice, e->st));
-    k_cast_copy<double><<<(int)((e->N + 255) / 256), 256, 0, e->st>>>(e->N, e->dtmp, e->tmpf);
-    double d, gm;
-    e->dissipation(e->tmpf, d, gm);
+    double d = 0.0, gm = 0.0;
+    int rc = h->e->dissipation_host(phi_host, d, gm);
     if (Dv) *Dv = d;
     if (Gv) *Gv = gm;
-    return RVE_OK;
+    return rc;
     GUARD_END
 }
 
-// Checkpoint layout: rve_scalars | curve length | curve | raw device buffers phi, H, psi_ini,
-// strain fluctuation, committed strain (internal precision and Mandel layout, so a reload
-// continues bit-exactly).
+// Checkpoint layout: rve_scalars | curve length | curve | raw device buffers (phi, H, psi_ini,
+// strain fluctuation in the handle's precision and Mandel layout, committed strain in FP64), so
+// a reload continues the load path bit-exactly.
 int rve_save(rve_handle h, void *buf, size_t *len) {
     if (!h || !len) return RVE_EINVAL;
     GUARD_BEGIN
-    auto *e = h->e64.get();
-    const size_t nf = (size_t)e->N * sizeof(double), nt = (size_t)e->NS * e->N * sizeof(double);
-    const size_t need = sizeof(rve_scalars) + sizeof(size_t) + e->curve.size() * sizeof(rve_step_result) + 3 * nf + 2 * nt;
+    auto *e = h->e.get();
+    const size_t need = sizeof(rve_scalars) + sizeof(size_t) + e->curve.size() * sizeof(rve_step_result) + e->state_bytes();
     if (!buf) { *len = need; return RVE_OK; }
     if (*len < need) return RVE_EINVAL;
     char *p = (char *)buf;
@@ -1357,10 +1462,7 @@ int rve_save(rve_handle h, void *buf, size_t *len) {
     size_t nc = e->curve.size();
     std::memcpy(p, &nc, sizeof(size_t)); p += sizeof(size_t);
     std::memcpy(p, e->curve.data(), nc * sizeof(rve_step_result)); p += nc * sizeof(rve_step_result);
-    const void *src[5] = {e->phi, e->H, e->psi_ini, e->mx, e->eps_com};
-    const size_t sz[5] = {nf, nf, nf, nt, nt};
-    for (int i = 0; i < 5; ++i) { CK(cudaMemcpyAsync(p, src[i], sz[i], cudaMemcpyDeviceToHost, e->st)); p += sz[i]; }
-    CK(cudaStreamSynchronize(e->st));
+    e->save_state(p);
     *len = need;
     return RVE_OK;
     GUARD_END
@@ -1369,24 +1471,19 @@ int rve_save(rve_handle h, void *buf, size_t *len) {
 int rve_load(rve_handle h, const void *buf, size_t len) {
     if (!h || !buf) return RVE_EINVAL;
     GUARD_BEGIN
-    auto *e = h->e64.get();
+    auto *e = h->e.get();
     if (!e->micro_set) return RVE_ESTATE;
-    const size_t nf = (size_t)e->N * sizeof(double), nt = (size_t)e->NS * e->N * sizeof(double);
     const char *p = (const char *)buf;
     if (len < sizeof(rve_scalars) + sizeof(size_t)) return RVE_EINVAL;
     rve_scalars s;
     std::memcpy(&s, p, sizeof(s)); p += sizeof(s);
     size_t nc;
     std::memcpy(&nc, p, sizeof(size_t)); p += sizeof(size_t);
-    const size_t need = sizeof(rve_scalars) + sizeof(size_t) + nc * sizeof(rve_step_result) + 3 * nf + 2 * nt;
+    const size_t need = sizeof(rve_scalars) + sizeof(size_t) + nc * sizeof(rve_step_result) + e->state_bytes();
     if (len != need) return RVE_EINVAL;
     std::vector<rve_step_result> cv(nc);
     std::memcpy(cv.data(), p, nc * sizeof(rve_step_result)); p += nc * sizeof(rve_step_result);
-    void *dst[5] = {e->phi, e->H, e->psi_ini, e->mx, e->eps_com};
-    const size_t sz[5] = {nf, nf, nf, nt, nt};
-    for (int i = 0; i < 5; ++i) { CK(cudaMemcpyAsync(dst[i], p, sz[i], cudaMemcpyHostToDevice, e->st)); p += sz[i]; }
-    CK(cudaMemcpyAsync(e->phi_trial, e->phi, nf, cudaMemcpyDeviceToDevice, e->st));
-    CK(cudaStreamSynchronize(e->st));
+    e->load_state(p);
     e->S = s;
     e->curve = cv;
     return RVE_OK;
@@ -1395,30 +1492,25 @@ int rve_load(rve_handle h, const void *buf, size_t len) {
 
 int rve_timing_enable(rve_handle h, int on) {
     if (!h) return RVE_EINVAL;
-    h->e64->timing = on != 0;
-    h->e64->ev_used = 0;
+    h->e->timing = on != 0;
+    h->e->timing_reset();
     return RVE_OK;
 }
 
 int rve_timing_get(rve_handle h, int kind, double *total_ms, long *launches, double *bytes_per_launch) {
     if (!h || kind != 0) return RVE_EINVAL;
     GUARD_BEGIN
-    auto *e = h->e64.get();
-    CK(cudaStreamSynchronize(e->st));
-    double tot = 0.0;
-    for (size_t i = 0; i < e->ev_used; ++i) {
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e->ev_pool[i].first, e->ev_pool[i].second));
-        tot += ms;
-    }
-    if (total_ms) *total_ms = tot;
-    if (launches) *launches = (long)e->ev_used;
-    if (bytes_per_launch) *bytes_per_launch = e->bytes_mech_axis;
+    double ms = 0.0, b = 0.0;
+    long n = 0;
+    h->e->timing_get(ms, n, b);
+    if (total_ms) *total_ms = ms;
+    if (launches) *launches = n;
+    if (bytes_per_launch) *bytes_per_launch = b;
     return RVE_OK;
     GUARD_END
 }
 
-long rve_launch_count(rve_handle h) { return h ? h->e64->launches : 0; }
+long rve_launch_count(rve_handle h) { return h ? h->e->launches : 0; }
 
 int rve_destroy(rve_handle h) {
     if (!h) return RVE_EINVAL;

@@ -80,56 +80,75 @@ struct ProCGDir : MechBase<T, NS> {
     __device__ Fin fin(Scal *) const { return Fin{}; }
 };
 
+// Frequency tables xi~ (Nyquist zeroed) per axis, in the field precision: x over the padded
+// half-spectrum columns (zero on padding), y and z over the full axes.
+template <typename R>
+struct XiTab {
+    const R *x, *y, *z;
+    __device__ __forceinline__ void get(int kx, int ky, int kz, R &a, R &b, R &c) const {
+        a = x[kx]; b = y[ky]; c = z[kz];
+    }
+};
+
+template <typename C> struct real_of;
+template <> struct real_of<double2> { typedef double type; };
+template <> struct real_of<float2> { typedef float type; };
+
+__device__ __forceinline__ double inv_sqrt(double v) { return 1.0 / sqrt(v); }
+__device__ __forceinline__ float inv_sqrt(float v) { return rsqrtf(v); }
+
 // Symmetric-strain Galerkin projection P^ = Gamma0(lambda0 = 0, mu0 = 1/2):
 // P(tau) = t (x) n + n (x) t - (n . t) n (x) n, t = tau n, n = xi~/|xi~|; zero where xi~ = 0.
 // On symmetric fields P(sigma) = 0 <=> G^ : sigma = 0 with G^ of Eq. (GFourier).
 template <typename C, int NS>
 struct OpProj {
+    typedef typename real_of<C>::type R;
     bool skip_if_done;
+    XiTab<R> xi;
     __device__ void apply(const Geom &g, int kx, int ky, int kz, const C *in, C *out) const {
-        const double xx = xi_of(kx, g.nx), xy = xi_of(ky, g.ny), xz = (g.nz > 1) ? xi_of(kz, g.nz) : 0.0;
-        const double q2 = xx * xx + xy * xy + xz * xz;
-        if (q2 == 0.0 || kx > (g.nx >> 1)) {
+        R xx, xy, xz;
+        xi.get(kx, ky, kz, xx, xy, xz);
+        const R q2 = xx * xx + xy * xy + xz * xz;
+        if (q2 == (R)0) {
 #pragma unroll
             for (int a = 0; a < NS; ++a) { out[a].x = 0; out[a].y = 0; }
             return;
         }
-        const double iq = 1.0 / sqrt(q2);
-        const double n0 = xx * iq, n1 = xy * iq, n2 = xz * iq;
-        const double r2 = 0.70710678118654752440;
+        const R iq = inv_sqrt(q2);
+        const R n0 = xx * iq, n1 = xy * iq, n2 = xz * iq;
+        const R r2 = (R)0.70710678118654752440, s2 = (R)1.41421356237309504880;
         if constexpr (NS == 3) {
-            // tensor components of tau (Mandel shear / sqrt2)
-            const double ax = in[0].x, ay = in[0].y, bx = in[1].x, by = in[1].y;
-            const double cx = in[2].x * r2, cy = in[2].y * r2;
-            const double t0x = ax * n0 + cx * n1, t0y = ay * n0 + cy * n1;
-            const double t1x = cx * n0 + bx * n1, t1y = cy * n0 + by * n1;
-            const double sx = t0x * n0 + t1x * n1, sy = t0y * n0 + t1y * n1;
+            const R ax = in[0].x, ay = in[0].y, bx = in[1].x, by = in[1].y;
+            const R cx = in[2].x * r2, cy = in[2].y * r2;
+            const R t0x = ax * n0 + cx * n1, t0y = ay * n0 + cy * n1;
+            const R t1x = cx * n0 + bx * n1, t1y = cy * n0 + by * n1;
+            const R sx = t0x * n0 + t1x * n1, sy = t0y * n0 + t1y * n1;
             out[0].x = 2 * t0x * n0 - sx * n0 * n0; out[0].y = 2 * t0y * n0 - sy * n0 * n0;
             out[1].x = 2 * t1x * n1 - sx * n1 * n1; out[1].y = 2 * t1y * n1 - sy * n1 * n1;
-            const double ox = t0x * n1 + t1x * n0 - sx * n0 * n1, oy = t0y * n1 + t1y * n0 - sy * n0 * n1;
-            out[2].x = ox * 1.41421356237309504880; out[2].y = oy * 1.41421356237309504880;
+            const R ox = t0x * n1 + t1x * n0 - sx * n0 * n1, oy = t0y * n1 + t1y * n0 - sy * n0 * n1;
+            out[2].x = ox * s2; out[2].y = oy * s2;
         } else {
-            double trx[3][3], tiy[3][3];
+            R trx[3][3], tiy[3][3];
             const int ii[6] = {0, 1, 2, 1, 0, 0}, jj[6] = {0, 1, 2, 2, 2, 1};
 #pragma unroll
             for (int a = 0; a < 6; ++a) {
-                const double w = a < 3 ? 1.0 : r2;
+                const R w = a < 3 ? (R)1 : r2;
                 trx[ii[a]][jj[a]] = trx[jj[a]][ii[a]] = in[a].x * w;
                 tiy[ii[a]][jj[a]] = tiy[jj[a]][ii[a]] = in[a].y * w;
             }
-            const double n[3] = {n0, n1, n2};
-            double tx[3], ty[3];
+            const R n[3] = {n0, n1, n2};
+            R tx[3], ty[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 tx[i] = trx[i][0] * n[0] + trx[i][1] * n[1] + trx[i][2] * n[2];
                 ty[i] = tiy[i][0] * n[0] + tiy[i][1] * n[1] + tiy[i][2] * n[2];
             }
-            const double sx = tx[0] * n[0] + tx[1] * n[1] + tx[2] * n[2];
-            const double sy = ty[0] * n[0] + ty[1] * n[1] + ty[2] * n[2];
+            const R sx = tx[0] * n[0] + tx[1] * n[1] + tx[2] * n[2];
+            const R sy = ty[0] * n[0] + ty[1] * n[1] + ty[2] * n[2];
 #pragma unroll
             for (int a = 0; a < 6; ++a) {
                 const int i = ii[a], j = jj[a];
-                const double w = a < 3 ? 1.0 : 1.41421356237309504880;
+                const R w = a < 3 ? (R)1 : s2;
                 out[a].x = w * (tx[i] * n[j] + n[i] * tx[j] - sx * n[i] * n[j]);
                 out[a].y = w * (ty[i] * n[j] + n[i] * ty[j] - sy * n[i] * n[j]);
             }
@@ -369,9 +388,12 @@ struct ProUpd {
 
 template <typename C, int D>
 struct OpGrad {  // 1 -> D: i xi~_a v^
+    typedef typename real_of<C>::type R;
     bool skip_if_done;
+    XiTab<R> xi;
     __device__ void apply(const Geom &g, int kx, int ky, int kz, const C *in, C *out) const {
-        const double xs[3] = {xi_of(kx, g.nx), xi_of(ky, g.ny), g.nz > 1 ? xi_of(kz, g.nz) : 0.0};
+        R xs[3];
+        xi.get(kx, ky, kz, xs[0], xs[1], xs[2]);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
             out[a].x = -xs[a] * in[0].y;
@@ -382,10 +404,13 @@ struct OpGrad {  // 1 -> D: i xi~_a v^
 
 template <typename C, int D>
 struct OpDiv {  // D -> 1: sum_a i xi~_a q^_a
+    typedef typename real_of<C>::type R;
     bool skip_if_done;
+    XiTab<R> xi;
     __device__ void apply(const Geom &g, int kx, int ky, int kz, const C *in, C *out) const {
-        const double xs[3] = {xi_of(kx, g.nx), xi_of(ky, g.ny), g.nz > 1 ? xi_of(kz, g.nz) : 0.0};
-        double ox = 0, oy = 0;
+        R xs[3];
+        xi.get(kx, ky, kz, xs[0], xs[1], xs[2]);
+        R ox = 0, oy = 0;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
             ox -= xs[a] * in[a].y;
@@ -398,11 +423,14 @@ struct OpDiv {  // D -> 1: sum_a i xi~_a q^_a
 
 template <typename C>
 struct OpPrec {  // v^ / (abar + bbar |xi~|^2)
+    typedef typename real_of<C>::type R;
     bool skip_if_done;
     const Scal *scr;
+    XiTab<R> xi;
     __device__ void apply(const Geom &g, int kx, int ky, int kz, const C *in, C *out) const {
-        const double a = xi_of(kx, g.nx), b = xi_of(ky, g.ny), c = g.nz > 1 ? xi_of(kz, g.nz) : 0.0;
-        const double s = 1.0 / (scr->abar + scr->bbar * (a * a + b * b + c * c));
+        R a, b, c;
+        xi.get(kx, ky, kz, a, b, c);
+        const R s = (R)1 / ((R)scr->abar + (R)scr->bbar * (a * a + b * b + c * c));
         out[0].x = in[0].x * s;
         out[0].y = in[0].y * s;
     }
@@ -537,18 +565,18 @@ struct EpiDiss {
     __device__ void apply(long long v, const T *gr, double *acc) const {
         const int gg = gid[v];
         const T *A = Atab + (size_t)gg * 6;
-        double q;
+        T q;
         if constexpr (D == 2) {
-            q = (double)gr[0] * (A[0] * gr[0] + A[2] * gr[1]) + (double)gr[1] * (A[2] * gr[0] + A[1] * gr[1]);
+            q = gr[0] * (A[0] * gr[0] + A[2] * gr[1]) + gr[1] * (A[2] * gr[0] + A[1] * gr[1]);
         } else {
-            q = (double)gr[0] * (A[0] * gr[0] + A[5] * gr[1] + A[4] * gr[2]) +
-                (double)gr[1] * (A[5] * gr[0] + A[1] * gr[1] + A[3] * gr[2]) +
-                (double)gr[2] * (A[4] * gr[0] + A[3] * gr[1] + A[2] * gr[2]);
+            q = gr[0] * (A[0] * gr[0] + A[5] * gr[1] + A[4] * gr[2]) +
+                gr[1] * (A[5] * gr[0] + A[1] * gr[1] + A[3] * gr[2]) +
+                gr[2] * (A[4] * gr[0] + A[3] * gr[1] + A[2] * gr[2]);
         }
-        const double p = (double)phi[v];
-        const double dens = p * p / (2.0 * ell) + 0.5 * ell * q;
-        acc[0] += (double)GcTab[gg] * dens;
-        acc[1] += dens;
+        const T p = phi[v];
+        const T dens = p * p / ((T)2 * (T)ell) + (T)0.5 * (T)ell * q;
+        acc[0] += (double)(GcTab[gg] * dens);
+        acc[1] += (double)dens;
     }
     struct Fin {
         Scal *sc;

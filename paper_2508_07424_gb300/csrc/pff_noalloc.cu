@@ -10,7 +10,8 @@
 // until the process exits.
 //
 // The computation is the same three fused passes the engine uses for D and Gamma:
-// the forward r2c FFT of phi, the spectral gradient i xi~ phi^, and the inverse c2r FFT with
+// the forward r2c FFT of phi, the spectral gradient i xi~ phi^ (frequency tables built in the
+// scratch array), and the inverse c2r FFT with
 // the reduction of sum Gc (phi^2/(2l) + l/2 grad phi . A grad phi).
 #include <cuda_runtime.h>
 
@@ -37,7 +38,7 @@ static void *g_scratch_addr[kMaxDevices] = {nullptr};
 static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t scal, partials, tw, spec, total;
+    size_t scal, partials, tw, xi, spec, total;
 };
 
 static int cw_of(int L) {
@@ -46,6 +47,20 @@ static int cw_of(int L) {
     if (cw > 16) cw = 16;
     if (cw < 2) cw = 2;
     return cw;
+}
+
+// Frequencies xi~ = 2 pi k / n (FFT order, Nyquist set to zero) on one axis; the x axis covers
+// the padded half-spectrum columns, whose padding gets zero.
+__global__ void k_xi(double *xi, int n, int len, int half) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= len) return;
+    const int lim = half ? n / 2 + 1 : n;
+    double v = 0.0;
+    if (k < lim && 2 * k != n) {
+        const int kk = k <= n / 2 ? k : k - n;
+        v = 6.283185307179586476925286766559 * (double)kk / (double)n;
+    }
+    xi[k] = v;
 }
 
 __global__ void k_twiddles(double2 *tw, int L) {
@@ -94,7 +109,8 @@ extern "C" int rve_dissipation_noalloc(int dim, const int n[3], double ell, int 
     lay.scal = 0;
     lay.partials = align256(sizeof(Scal));
     lay.tw = lay.partials + align256(sizeof(double) * 2 * (size_t)xblocks);
-    lay.spec = lay.tw + align256(sizeof(double2) * (size_t)(nx + ny + nz));
+    lay.xi = lay.tw + align256(sizeof(double2) * (size_t)(nx + ny + nz));
+    lay.spec = lay.xi + align256(sizeof(double) * (size_t)(g.Px + ny + nz));
     lay.total = lay.spec + align256(sizeof(double2) * (size_t)dim * (size_t)g.Nh);
     if (lay.total > kScratchBytes) {
         std::fprintf(stderr,
@@ -118,6 +134,10 @@ extern "C" int rve_dissipation_noalloc(int dim, const int n[3], double ell, int 
     double2 *twx = (double2 *)(base + lay.tw);
     double2 *twy = twx + nx;
     double2 *twz = twy + ny;
+    double *xix = (double *)(base + lay.xi);
+    double *xiy = xix + g.Px;
+    double *xiz = xiy + ny;
+    const XiTab<double> xi{xix, xiy, xiz};
     double2 *spec = (double2 *)(base + lay.spec);
     cudaStream_t st = (cudaStream_t)stream;
 
@@ -128,6 +148,9 @@ extern "C" int rve_dissipation_noalloc(int dim, const int n[3], double ell, int 
     k_twiddles<<<(nx + 255) / 256, 256, 0, st>>>(twx, nx);
     k_twiddles<<<(ny + 255) / 256, 256, 0, st>>>(twy, ny);
     if (nz > 1) k_twiddles<<<(nz + 255) / 256, 256, 0, st>>>(twz, nz);
+    k_xi<<<(g.Px + 255) / 256, 256, 0, st>>>(xix, nx, g.Px, 1);
+    k_xi<<<(ny + 255) / 256, 256, 0, st>>>(xiy, ny, ny, 0);
+    k_xi<<<(nz + 255) / 256, 256, 0, st>>>(xiz, nz, nz, 0);
 
     const size_t smx = (size_t)RP * nx * sizeof(double2);
     auto axis_launch = [&](auto kernel, int ax, int NM, const auto &op, const double2 *tw) -> cudaError_t {
@@ -147,18 +170,18 @@ extern "C" int rve_dissipation_noalloc(int dim, const int n[3], double ell, int 
     }
     const int32_t *gid = grain_id;
     if (dim == 2) {
-        if (axis_launch(k_axis<double, 1, 2, AX_FWD_OP_INV, OpGrad<double2, 2>>, 1, 2, OpGrad<double2, 2>{false}, twy))
+        if (axis_launch(k_axis<double, 1, 2, AX_FWD_OP_INV, OpGrad<double2, 2>>, 1, 2, OpGrad<double2, 2>{false, xi}, twy))
             return RVE_ECUDA;
         auto k = k_x_inv<double, 2, EpiDiss<double, 2>>;
         const size_t sm = smx * 2;
         if (sm > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k<<<xblocks, xthreads, sm, st>>>(g, spec, EpiDiss<double, 2>{false, phi, Gc, A, gid, ell}, twx, partials, sc);
     } else {
-        if (axis_launch(k_axis<double, 1, 1, AX_FWD, OpGrad<double2, 3>>, 1, 1, OpGrad<double2, 3>{false}, twy))
+        if (axis_launch(k_axis<double, 1, 1, AX_FWD, OpGrad<double2, 3>>, 1, 1, OpGrad<double2, 3>{false, xi}, twy))
             return RVE_ECUDA;
-        if (axis_launch(k_axis<double, 1, 3, AX_FWD_OP_INV, OpGrad<double2, 3>>, 2, 3, OpGrad<double2, 3>{false}, twz))
+        if (axis_launch(k_axis<double, 1, 3, AX_FWD_OP_INV, OpGrad<double2, 3>>, 2, 3, OpGrad<double2, 3>{false, xi}, twz))
             return RVE_ECUDA;
-        if (axis_launch(k_axis<double, 3, 3, AX_INV, OpGrad<double2, 3>>, 1, 3, OpGrad<double2, 3>{false}, twy))
+        if (axis_launch(k_axis<double, 3, 3, AX_INV, OpGrad<double2, 3>>, 1, 3, OpGrad<double2, 3>{false, xi}, twy))
             return RVE_ECUDA;
         auto k = k_x_inv<double, 3, EpiDiss<double, 3>>;
         const size_t sm = smx * 3;
