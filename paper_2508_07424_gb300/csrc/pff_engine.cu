@@ -399,6 +399,95 @@ __global__ void k_cast_copy(long long n, const double *src, T *dst) {
     if (v < n) dst[v] = (T)src[v];
 }
 
+// eps_k = f + x (Newton linearisation point of the split equilibrium).
+template <typename T>
+struct PwEpsK {
+    static constexpr int NR = 0;
+    static constexpr bool MAXRED = false;
+    bool skip_if_done;
+    const T *x;
+    T *epsk;
+    T f[3];
+    long long N;
+    __device__ void apply(long long v, double *) const {
+        for (int a = 0; a < 3; ++a) epsk[a * N + v] = f[a] + x[a * N + v];
+    }
+    struct Fin { __device__ void operator()(const double *) const {} };
+    __device__ Fin fin(Scal *) const { return Fin{}; }
+};
+
+// Inner (Newton) CG stopping test relative to the initial residual.
+__global__ void k_inner_tol(Scal *sc, double eta2) {
+    if (!sc->done) { sc->tol2 = eta2; sc->scale2 = sc->rr0; }
+}
+
+// psi1 = psi+(f + x): the crack driving energy with the split.
+template <typename T>
+struct PwPsi1Split {
+    static constexpr int NR = 0;
+    static constexpr bool MAXRED = false;
+    bool skip_if_done;
+    const T *x, *lam, *mu;
+    const int *gid;
+    T *psi1;
+    T f[3];
+    long long N;
+    __device__ void apply(long long v, double *) const {
+        T e[3], sp[3], sm[3], pp, pm;
+        for (int a = 0; a < 3; ++a) e[a] = f[a] + x[a * N + v];
+        const int g = gid[v];
+        split_sigma(e, lam[g], mu[g], sp, sm, pp, pm);
+        psi1[v] = pp;
+    }
+    struct Fin { __device__ void operator()(const double *) const {} };
+    __device__ Fin fin(Scal *) const { return Fin{}; }
+};
+
+// Committed Sigma = <sigma(E eps1)> : f = E <g sigma+(eps1) + sigma-(eps1)> : f and
+// E_mec = E^2 sum (g psi+(eps1) + psi-(eps1)) (the split is positively homogeneous).
+template <typename T>
+struct PwCommitSplit {
+    static constexpr int NR = 2;
+    static constexpr bool MAXRED = false;
+    bool skip_if_done;
+    const T *x, *phi, *lam, *mu;
+    const int *gid;
+    double f[3];
+    double E, k;
+    long long N;
+    __device__ void apply(long long v, double *acc) const {
+        double e[3], sp[3], sm[3], pp, pm;
+        for (int a = 0; a < 3; ++a) e[a] = f[a] + (double)x[a * N + v];
+        const int g = gid[v];
+        split_sigma(e, (double)lam[g], (double)mu[g], sp, sm, pp, pm);
+        const double ph = (double)phi[v];
+        const double gp = (1.0 - ph) * (1.0 - ph) + k;
+        double sf = 0.0;
+        for (int a = 0; a < 3; ++a) sf += (gp * sp[a] + sm[a]) * f[a];
+        acc[0] += E * sf;
+        acc[1] += E * E * (gp * pp + pm);
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const { sc->red[4] = t[0]; sc->red[5] = t[1]; }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+template <typename T>
+__global__ void k_stress_split(long long N, const T *lam, const T *mu, const int *gid, const T *phi, double k,
+                               const double *eps, double *sig) {
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= N) return;
+    double e[3], sp[3], sm[3], pp, pm;
+    for (int a = 0; a < 3; ++a) e[a] = eps[a * N + v];
+    const int g = gid[v];
+    split_sigma(e, (double)lam[g], (double)mu[g], sp, sm, pp, pm);
+    const double ph = (double)phi[v];
+    const double gp = (1.0 - ph) * (1.0 - ph) + k;
+    for (int a = 0; a < 3; ++a) sig[a * N + v] = gp * sp[a] + sm[a];
+}
+
 template <typename C> struct OpNone {
     bool skip_if_done;
     __device__ void apply(const Geom &, int, int, int, const C *, C *) const {}
@@ -775,7 +864,56 @@ struct Engine : EngineBase {
         return RVE_OK;
     }
     int mech_solve(const T *phi_in, int &iters) {
+        if (cfg.split == RVE_SPLIT_SPECTRAL) return mech_solve_split(phi_in, iters);
         return NS == 3 ? mech_solve_t<3>(phi_in, iters) : mech_solve_t<6>(phi_in, iters);
+    }
+
+    // Equilibrium with the spectral split (2D): Newton on P[sigma(f + x)] = 0, each step a CG on
+    // the tangent P[K(eps_k) : dx] = -P[sigma(eps_k)] to 1e-3 of its initial residual; stops when
+    // |P[sigma]| <= tol_mech |sigma|. The problem is positively homogeneous of degree one, so the
+    // unit-load solution scales with E >= 0.
+    T *epsk = nullptr;
+    int mech_solve_split(const T *phi_in, int &iters) {
+        if (!epsk) epsk = alloc<T>((size_t)3 * N);
+        ProSplitStress<T> pst{true, mx, phi_in, lamT, muT, gid, (T)cfg.k_res, {}, N};
+        for (int a = 0; a < 3; ++a) pst.f[a] = (T)fM[a];
+        OpProj<C, 3> proj{true, xitab()};
+        PwEpsK<T> ek{false, mx, epsk, {}, N};
+        for (int a = 0; a < 3; ++a) ek.f[a] = (T)fM[a];
+        ProSplitDir<T> dir{true, mr, epsk, phi_in, lamT, muT, mp, gid, (T)cfg.k_res, sc, N};
+        EpiMechQ<T, 3> eq{true, mq, mp, N};
+        PwMechUpdate<T, 3> up{true, mx, mr, mp, mq, sc, N};
+        iters = 0;
+        for (int newton = 0; newton < 100; ++newton) {
+            init_sc(sc, cfg.tol_mech, std::max(1, cfg.max_mech_iters - iters));
+            x_fwd<3>(pst, sc);
+            spectral<3, 3>(proj, sc, true);
+            x_inv<3>(EpiMechInit<T, 3>{true, mr, N}, sc);
+            read_sc(sc);
+            if (h_sc->flag) return RVE_EBREAKDOWN;
+            if (h_sc->done) break;
+            pointwise(ek, sc);
+            k_inner_tol<<<1, 1, 0, st>>>(sc, 1e-6);
+            ++launches;
+            for (;;) {
+                for (int c = 0; c < 8; ++c) {
+                    x_fwd<3>(dir, sc);
+                    spectral<3, 3>(proj, sc, true);
+                    x_inv<3>(eq, sc);
+                    pointwise(up, sc);
+                }
+                read_sc(sc);
+                if (h_sc->done) break;
+            }
+            iters += h_sc->iters;
+            if (h_sc->flag) return RVE_EBREAKDOWN;
+            if (iters >= cfg.max_mech_iters) return RVE_ENOCONV;
+            if (newton == 99) return RVE_ENOCONV;
+        }
+        PwPsi1Split<T> ps{false, mx, lamT, muT, gid, psi1, {}, N};
+        for (int a = 0; a < 3; ++a) ps.f[a] = (T)fM[a];
+        pointwise(ps, sc);
+        return RVE_OK;
     }
 
     // ---- damage (a6-a8) ------------------------------------------------------------------------
@@ -1138,7 +1276,11 @@ struct Engine : EngineBase {
         CK(cudaMemcpyAsync(H, Hcur, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(eps_com, eps_it, sizeof(double) * NS * N, cudaMemcpyDeviceToDevice, st));
         init_sc(sc2, 0, 0);
-        if (NS == 3) {
+        if (cfg.split == RVE_SPLIT_SPECTRAL) {
+            PwCommitSplit<T> pc{false, mx, phi, lamT, muT, gid, {}, E, cfg.k_res, N};
+            for (int a = 0; a < 3; ++a) pc.f[a] = fM[a];
+            pointwise(pc, sc2);
+        } else if (NS == 3) {
             PwCommit<T, 3> pc{false, Cm, mx, phi, psi1, gid, {}, E, cfg.k_res, N};
             for (int a = 0; a < 3; ++a) pc.f[a] = fM[a];
             pointwise(pc, sc2);
@@ -1243,7 +1385,10 @@ struct Engine : EngineBase {
                 k_mandel_to_tensor<double><<<blocks, 256, 0, st>>>(N, D, eps_com, 1.0, nullptr, dtmp);
             } else {
                 double *sig = alloc_tmp_sig();
-                k_stress<T><<<blocks, 256, 0, st>>>(N, D, Cm, gid, phi, cfg.k_res, eps_com, sig);
+                if (cfg.split == RVE_SPLIT_SPECTRAL)
+                    k_stress_split<T><<<blocks, 256, 0, st>>>(N, lamT, muT, gid, phi, cfg.k_res, eps_com, sig);
+                else
+                    k_stress<T><<<blocks, 256, 0, st>>>(N, D, Cm, gid, phi, cfg.k_res, eps_com, sig);
                 k_mandel_to_tensor<double><<<blocks, 256, 0, st>>>(N, D, sig, 1.0, nullptr, dtmp);
             }
             break;
@@ -1345,7 +1490,8 @@ int rve_create(const rve_config *cfg, rve_handle *out) {
     if (cfg->dim == 3 && !pow2_in(cfg->n[2], 4, 1024)) return RVE_EINVAL;
     if ((long long)cfg->n[0] * cfg->n[1] * cfg->n[2] > (1LL << 24)) return RVE_EINVAL;
     if (!(cfg->ell > 0) || cfg->k_res < 0 || cfg->anderson_m < 0 || cfg->anderson_m > 5) return RVE_EINVAL;
-    if (cfg->split == RVE_SPLIT_SPECTRAL) return RVE_EINVAL;  // spectral split: not yet on the GPU path
+    if (cfg->split != RVE_SPLIT_NONE && cfg->split != RVE_SPLIT_SPECTRAL) return RVE_EINVAL;
+    if (cfg->split == RVE_SPLIT_SPECTRAL && cfg->dim != 2) return RVE_EINVAL;  // split: plane strain only
     if (cfg->precision != RVE_FP64 && cfg->precision != RVE_FP32R) return RVE_EINVAL;
     GUARD_BEGIN
     auto *h = new rve_s();

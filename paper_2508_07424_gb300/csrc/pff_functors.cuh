@@ -80,6 +80,143 @@ struct ProCGDir : MechBase<T, NS> {
     __device__ Fin fin(Scal *) const { return Fin{}; }
 };
 
+// ---- spectral tension/compression split (2D plane strain, isotropic lam, mu) ---------------------
+// eps = (a, b, sqrt2 c) in Mandel form, eps_zz = 0. In-plane eigenvalues e1,2 = (a+b)/2 +- r,
+// r = sqrt(((a-b)/2)^2 + c^2), eigenvectors at angle theta with cos 2theta = (a-b)/(2r),
+// sin 2theta = c/r. psi+- = lam/2 <tr>+-^2 + mu sum <e_a>+-^2, sigma+- = lam <tr>+- I + 2 mu eps+-;
+// the tangent uses the divided differences of <.>+- over the eigenvalue pairs.
+template <typename T>
+struct SplitState {
+    T e1, e2, tr, C2, S2;  // eigenvalues, trace, cos 2theta, sin 2theta
+};
+
+template <typename T> __device__ __forceinline__ SplitState<T> split_eig(const T *em) {
+    const T r2 = (T)0.70710678118654752440;
+    const T a = em[0], b = em[1], c = em[2] * r2;
+    const T d = (T)0.5 * (a - b);
+    const T r = sqrt(d * d + c * c);
+    SplitState<T> st;
+    st.tr = a + b;
+    st.e1 = (T)0.5 * st.tr + r;
+    st.e2 = (T)0.5 * st.tr - r;
+    if (r > (T)0) { st.C2 = d / r; st.S2 = c / r; }
+    else { st.C2 = (T)1; st.S2 = (T)0; }
+    return st;
+}
+
+template <typename T> __device__ __forceinline__ T pos_(T x) { return x > (T)0 ? x : (T)0; }
+template <typename T> __device__ __forceinline__ T neg_(T x) { return x < (T)0 ? x : (T)0; }
+
+// sigma+ and sigma- (Mandel) and psi+, psi- at eps (Mandel).
+template <typename T>
+__device__ __forceinline__ void split_sigma(const T *em, T lam, T mu, T *sp, T *sm, T &psp, T &psm) {
+    const SplitState<T> q = split_eig(em);
+    const T s2 = (T)1.41421356237309504880;
+    // n1 n1 = 1/2 [1 + C2, S2; S2, 1 - C2], n2 n2 = 1/2 [1 - C2, -S2; -S2, 1 + C2]
+    const T p1 = pos_(q.e1), p2 = pos_(q.e2), m1 = neg_(q.e1), m2 = neg_(q.e2);
+    const T tp = pos_(q.tr), tm = neg_(q.tr);
+    const T epxx = (T)0.5 * (p1 * ((T)1 + q.C2) + p2 * ((T)1 - q.C2));
+    const T epyy = (T)0.5 * (p1 * ((T)1 - q.C2) + p2 * ((T)1 + q.C2));
+    const T epxy = (T)0.5 * (p1 - p2) * q.S2;
+    const T emxx = (T)0.5 * (m1 * ((T)1 + q.C2) + m2 * ((T)1 - q.C2));
+    const T emyy = (T)0.5 * (m1 * ((T)1 - q.C2) + m2 * ((T)1 + q.C2));
+    const T emxy = (T)0.5 * (m1 - m2) * q.S2;
+    sp[0] = lam * tp + 2 * mu * epxx; sp[1] = lam * tp + 2 * mu * epyy; sp[2] = s2 * 2 * mu * epxy;
+    sm[0] = lam * tm + 2 * mu * emxx; sm[1] = lam * tm + 2 * mu * emyy; sm[2] = s2 * 2 * mu * emxy;
+    psp = (T)0.5 * lam * tp * tp + mu * (p1 * p1 + p2 * p2);
+    psm = (T)0.5 * lam * tm * tm + mu * (m1 * m1 + m2 * m2);
+}
+
+// Directional derivative of sigma = g sigma+ + sigma- at eps along dm (both Mandel).
+template <typename T>
+__device__ __forceinline__ void split_tangent(const T *em, const T *dm, T lam, T mu, T g, T *out) {
+    const SplitState<T> q = split_eig(em);
+    const T r2 = (T)0.70710678118654752440, s2 = (T)1.41421356237309504880;
+    const T c = sqrt(fmax((T)0, (T)0.5 * ((T)1 + q.C2)));
+    const T sn = copysign(sqrt(fmax((T)0, (T)0.5 * ((T)1 - q.C2))), q.S2);
+    const T dxx = dm[0], dyy = dm[1], dxy = dm[2] * r2;
+    const T cs = c * sn, cc = c * c, ss = sn * sn;
+    const T P11 = cc * dxx + 2 * cs * dxy + ss * dyy;
+    const T P22 = ss * dxx - 2 * cs * dxy + cc * dyy;
+    const T P12 = -cs * dxx + (cc - ss) * dxy + cs * dyy;
+    const T trd = dxx + dyy;
+    T res[3] = {0, 0, 0};
+    for (int part = 0; part < 2; ++part) {
+        const bool plus = part == 0;
+        const T f1 = plus ? pos_(q.e1) : neg_(q.e1), f2 = plus ? pos_(q.e2) : neg_(q.e2);
+        const T d1 = plus ? (T)(q.e1 > 0) : (T)(q.e1 < 0), d2 = plus ? (T)(q.e2 > 0) : (T)(q.e2 < 0);
+        const T qq = (q.e1 == q.e2) ? d1 : (f1 - f2) / (q.e1 - q.e2);
+        const T ht = plus ? (T)(q.tr > 0) : (T)(q.tr < 0);
+        // DF = d1 P11 n1n1 + d2 P22 n2n2 + qq P12 (n1n2 + n2n1)
+        const T Fxx = (T)0.5 * (d1 * P11 * ((T)1 + q.C2) + d2 * P22 * ((T)1 - q.C2)) - qq * P12 * q.S2;
+        const T Fyy = (T)0.5 * (d1 * P11 * ((T)1 - q.C2) + d2 * P22 * ((T)1 + q.C2)) + qq * P12 * q.S2;
+        const T Fxy = (T)0.5 * (d1 * P11 - d2 * P22) * q.S2 + qq * P12 * q.C2;
+        const T w = plus ? g : (T)1;
+        res[0] += w * (lam * ht * trd + 2 * mu * Fxx);
+        res[1] += w * (lam * ht * trd + 2 * mu * Fyy);
+        res[2] += w * (2 * mu * Fxy);
+    }
+    out[0] = res[0]; out[1] = res[1]; out[2] = s2 * res[2];
+}
+
+// s = sigma(f + x) with the split; reduces |sigma|^2 (the scale of the Newton stopping test).
+template <typename T>
+struct ProSplitStress {
+    static constexpr int NR = 1;
+    bool skip_if_done;
+    const T *x, *phi, *lam, *mu;
+    const int *gid;
+    T k;
+    T f[3];
+    long long N;
+    __device__ void eval(long long v, T *out, double *acc) const {
+        T e[3], sp[3], sm[3], pp, pm;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) e[a] = f[a] + x[a * N + v];
+        const int g = gid[v];
+        split_sigma(e, lam[g], mu[g], sp, sm, pp, pm);
+        const T gp = degr(phi[v], k);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            out[a] = gp * sp[a] + sm[a];
+            acc[0] += (double)out[a] * (double)out[a];
+        }
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const { sc->scale2 = t[0]; }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+// Newton CG direction p = r + beta p fused with s = K(eps_k) : p (tangent frozen at eps_k).
+template <typename T>
+struct ProSplitDir {
+    static constexpr int NR = 0;
+    bool skip_if_done;
+    const T *r, *epsk, *phi, *lam, *mu;
+    T *p;
+    const int *gid;
+    T k;
+    const Scal *scr;
+    long long N;
+    __device__ void eval(long long v, T *out, double *) const {
+        const T beta = (T)scr->beta;
+        T u[3], e[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const size_t i = a * N + v;
+            u[a] = r[i] + beta * p[i];
+            p[i] = u[a];
+            e[a] = epsk[i];
+        }
+        const int g = gid[v];
+        split_tangent(e, u, lam[g], mu[g], degr(phi[v], k), out);
+    }
+    struct Fin { __device__ void operator()(const double *) const {} };
+    __device__ Fin fin(Scal *) const { return Fin{}; }
+};
+
 // Frequency tables xi~ (Nyquist zeroed) per axis, in the field precision: x over the padded
 // half-spectrum columns (zero on padding), y and z over the full axes.
 template <typename R>

@@ -226,3 +226,57 @@ def test_fp32r_equilibrium_solve(cap):
     g_eps = sym_components(model.fB, model.d) + g.get(cap.RVE_FIELD_FLUCT1)
     # FP32 residual floor 1e-6 x the conditioning of this random-damage RVE (contrast ~100)
     assert rel(g_eps, sym_components(eps, model.d)) < 5e-5
+
+
+# ---- spectral energy split (configs[0] model variant; plane strain) ------------------------------
+def _split_case():
+    w = synth.small_cases()["homog32"]
+    return synth.replace(w, split=1)
+
+
+def test_split_equilibrium_solve(cap):
+    from paper_2508_07424_gb300.rve import Rve
+    w = _split_case()
+    model = S.Model(w.micro, S.params_from_workload(w, tol_mech=1e-12))
+    g = Rve.from_workload(w, tol_mech=1e-12)
+    rng = np.random.default_rng(8)
+    phi = rng.uniform(0.0, 0.9, model.grid)
+    g.set(cap.RVE_FIELD_PHI, phi)
+    g.mech_solve()
+    F1, _ = S.mech_solve(model, phi, np.zeros((2, 2) + model.grid))
+    ref = sym_components(F1, 2)
+    assert rel(g.get(cap.RVE_FIELD_FLUCT1), ref) < 1e-9
+    eps1 = model.fB + tensor_from_components(ref, 2)
+    assert rel(g.get(cap.RVE_FIELD_PSI1), model.drive(eps1)) < 1e-9
+
+
+def test_split_increments(cap):
+    from paper_2508_07424_gb300.rve import Rve
+    w = _split_case()
+    model = S.Model(w.micro, S.params_from_workload(w, tol_stag=1e-11))
+    g = Rve.from_workload(w, tol_stag=1e-11)
+    st = S.init_state(model)
+    for _ in range(3):
+        st, _ = S.increment(model, st, w.dtau)
+        r = g.step(w.dtau)
+        o = st.curve[-1]
+        for k in ("E", "Sigma", "D", "T", "Emec"):
+            assert abs(r[k] - o[k]) <= 1e-9 * abs(o[k]), (k, r[k], o[k])
+    sig = sym_components(model.stress(st.eps, st.phi), 2)
+    assert rel(g.get(cap.RVE_FIELD_SIGMA), sig) < 1e-9
+    assert rel(g.get(cap.RVE_FIELD_PHI), st.phi) < 1e-9
+
+
+def test_homogeneous_plate_64_with_split_first_increment(cap):
+    """The 64^2 homogeneous plate with the spectral split and a 16-voxel CTE crack (the small
+    workload of the benchmark set), first increment against the oracle."""
+    from paper_2508_07424_gb300.rve import Rve
+    w = synth.homogeneous_plate_64()
+    model = S.Model(w.micro, S.params_from_workload(w, tol_stag=1e-10))
+    g = Rve.from_workload(w, tol_stag=1e-10)
+    st = S.init_state(model)
+    st, _ = S.increment(model, st, w.dtau)
+    r = g.step(w.dtau)
+    o = st.curve[-1]
+    for k in ("E", "Sigma", "D", "T"):
+        assert abs(r[k] - o[k]) <= 1e-9 * abs(o[k]), (k, r[k], o[k])
