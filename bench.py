@@ -251,7 +251,90 @@ def run_gpu(args):
     }
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(args, timed_steps=1)
+    if args.precision == "fp32r" and world == 1:
+        out["fp64_side_by_side"] = side_by_side_fp64(args, stream)
+    if not args.no_serve and world == 1:
+        out["serving"] = serving(args)
     return out
+
+
+def side_by_side_fp64(args, stream):
+    """The plain FP64 path on the same RVE and increments (3 warm-up, then 3 timed increments)."""
+    import torch
+
+    from paper_2508_07424_gb300.rve import Rve
+    w = make_workload(0, "fp64")
+    g = Rve.from_workload(w, stream=stream.cuda_stream, **solver_tols("fp64"))
+    for _ in range(3):
+        g.step(w.dtau)
+    torch.cuda.synchronize()
+    a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    vu = 0
+    for _ in range(3):
+        r = g.step(w.dtau)
+        vu += (r["mech_iters"] + r["dmg_iters"]) * g.nvox
+    b_.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b_)
+    g.close()
+    return {"value": vu / (ms * 1e-3), "unit": "voxel-updates/s", "ms_per_step": ms / 3, "dtype": "f64",
+            "steps": 3, "warmup": 3}
+
+
+def serving(args):
+    """Continuous batching vs one-by-one: the same seeded request mix (2D 64^2-256^2 and 3D 32^3,
+    fibre composites and polycrystals, a fixed number of increments each) is first run one by
+    one on the plain FP64 path; its measured rate r sets Poisson arrivals at 1.25 r, replayed
+    through the native request server (FP32 with refinement, 8 slots, admission by footprint)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2508_07424_gb300 import serve
+    from paper_2508_07424_gb300.rve import Rve
+    ws = synth.serving_mix(count=args.serve_requests, n_inc=args.serve_inc)
+    # plain FP64, one by one
+    serial, plain_failed = [], []
+    for i, w in enumerate(ws):
+        t0 = time.perf_counter()
+        g = Rve.from_workload(synth.replace(w, precision="fp64"), tol_stag=1e-8)
+        try:
+            for _ in range(w.n_inc):
+                if g.step(w.dtau)["fractured"]:
+                    break
+        except Exception as e:  # a request that fails is retired, as in the server
+            plain_failed.append({"request": i, "grid": list(w.micro.n), "name": w.name, "error": str(e)})
+        g.close()
+        serial.append(time.perf_counter() - t0)
+    rate_plain = len(ws) / sum(serial)
+    lam = 1.25 * rate_plain
+    arrivals = np.cumsum(np.random.default_rng(40).exponential(1.0 / lam, len(ws)))
+    arrivals -= arrivals[0]
+    # the plain path on the same arrival trace (a single FIFO server)
+    fin, lat_plain = 0.0, []
+    for ta, sv in zip(arrivals, serial):
+        fin = max(fin, ta) + sv
+        lat_plain.append(fin - ta)
+    free, _ = torch.cuda.mem_get_info()
+    srv = serve.Server(max_inflight=8, hbm_budget_bytes=int(0.5 * free))
+    reqs = [(float(ta), synth.replace(w, precision="fp32r"), w.n_inc) for ta, w in zip(arrivals, ws)]
+    out, wall = serve.replay(srv, reqs)
+    st = srv.stats()
+    srv.close()
+    ok = [r for r in out.values() if r["status"] == 0]
+    lat = [r["t_end"] - r["t_submit"] for r in ok]
+    return {"requests": len(ws), "increments_per_request": args.serve_inc,
+            "mix": "2D {64,128,256}^2 fibre/polycrystal + 3D 32^3 polycrystal, seeded (synth.serving_mix)",
+            "arrivals": f"Poisson, rate 1.25 x plain FP64 one-by-one rate ({lam:.3f}/s)",
+            "solves_per_s": len(ok) / wall, "p50_s": serve.percentile(lat, 0.5), "p99_s": serve.percentile(lat, 0.99),
+            "failed": [{"request": r["id"], "status": r["status"], "grid": list(ws[r["id"]].micro.n),
+                        "name": ws[r["id"]].name} for r in out.values() if r["status"] != 0],
+            "voxel_updates_per_s": sum(r["voxel_updates"] for r in ok) / wall,
+            "peak_inflight": st["peak_inflight"], "slots": 8, "precision": "fp32r",
+            "plain_fp64_one_by_one": {"solves_per_s": rate_plain, "p50_s": serve.percentile(lat_plain, 0.5),
+                                      "p99_s": serve.percentile(lat_plain, 0.99),
+                                      "service_p50_s": serve.percentile(serial, 0.5), "failed": plain_failed}}
 
 
 def oracle_sample(rank=0, iters=60):
@@ -323,10 +406,13 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32r"])
+    ap.add_argument("--precision", default="fp32r", choices=["fp64", "fp32r"])
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-inc", type=int, default=15)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     out = run_reference(args) if args.impl == "reference" else run_gpu(args)

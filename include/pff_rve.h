@@ -177,6 +177,39 @@ long rve_launch_count(rve_handle h);
 int rve_destroy(rve_handle h);
 const char *rve_strerror(int status);
 
+/* ---- serving: many RVE toughness solves on one GPU --------------------------------------------
+ * A request is one RVE broken by dissipation increments (Sec. 4.1-4.2) until the fracture point
+ * F or n_inc increments; its result carries the effective toughness of Eqs. (JaviGc)/(ABC) when
+ * F was reached. Worker threads run admitted requests concurrently, each on its own handle and
+ * CUDA stream, so the work of different RVEs overlaps on the device; admission is first come
+ * first served under max_inflight slots and an HBM budget checked against rve_footprint_bytes
+ * (a request larger than the budget runs alone). A failing request is retired with its status
+ * and the others keep running. Times are seconds since rve_server_create. */
+typedef struct rve_server_s *rve_server;
+
+typedef struct {
+    long id;                 /* the id given at submission */
+    int status;              /* RVE_OK or the first error of the request */
+    int fractured;           /* 1 if the fracture point was reached */
+    int n_done;              /* increments completed */
+    double toughness;        /* G_Ceff when fractured, NaN otherwise */
+    double E_last, Sigma_last, T_last, Sigma_max;
+    double t_submit, t_start, t_end;
+    long voxel_updates;      /* sum over increments of (CG + PCG iterations) x voxels */
+} rve_request_result;
+
+/* Device bytes one handle with this configuration holds (estimate used for admission). */
+size_t rve_footprint_bytes(const rve_config *cfg);
+/* max_inflight in [1, 256]; hbm_budget_bytes: admission budget over concurrently held footprints. */
+int rve_server_create(int max_inflight, size_t hbm_budget_bytes, rve_server *out);
+/* cfg and m are copied (cfg->stream is ignored). n_inc >= 1, dtau > 0. */
+int rve_server_submit(rve_server s, long id, const rve_config *cfg, const rve_micro *m, int n_inc, double dtau);
+/* Collect up to max finished results; waits up to timeout_s seconds for at least one (0: poll). */
+int rve_server_wait(rve_server s, rve_request_result *out, int max, double timeout_s, int *n_out);
+int rve_server_stats(rve_server s, int *peak_inflight, size_t *peak_bytes, long *pending);
+/* Finishes every submitted request, then joins the workers. */
+int rve_server_destroy(rve_server s);
+
 /* Allocation-free D(phi) and Gamma(phi), for callers that cannot allocate device memory when
  * they need the value (a framework that owns all device memory through its own pool, a
  * latency-critical loop that must not hit the implicit synchronisation of cudaMalloc/cudaFree,

@@ -6,7 +6,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libpff_gb300.so")
-SOURCES = [os.path.join(HERE, "csrc", f) for f in ("pff_engine.cu", "pff_noalloc.cu")]
+SOURCES = [os.path.join(HERE, "csrc", f) for f in ("pff_engine.cu", "pff_noalloc.cu", "pff_serve.cu")]
 HEADERS = [os.path.join(HERE, "csrc", f) for f in ("pff_common.cuh", "pff_kernels.cuh", "pff_functors.cuh")] + [
     os.path.join(ROOT, "include", "pff_rve.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -29,11 +29,25 @@ def up_to_date():
 def build(force=False, verbose=False):
     if not force and up_to_date():
         return LIB
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-o", LIB + ".tmp", *SOURCES]
+    # translation units compile in parallel, then one link step
+    from concurrent.futures import ThreadPoolExecutor
+    objdir = os.path.join(HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
+
+    def compile_one(src):
+        obj = os.path.join(objdir, os.path.basename(src) + ".o")
+        r = subprocess.run([nvcc(), *flags, "-c", "-o", obj, src], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src}:\n" + r.stdout + r.stderr)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES))
+    cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", LIB + ".tmp", *objs, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
+        raise RuntimeError("nvcc link failed:\n" + r.stdout + r.stderr)
     os.replace(LIB + ".tmp", LIB)
     if verbose:
         print(" ".join(cmd))

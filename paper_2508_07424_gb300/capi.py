@@ -42,7 +42,15 @@ class rve_scalars(C.Structure):
                 ("Sigma", C.c_double), ("Sigma_max", C.c_double), ("tau0", C.c_double), ("fractured", C.c_int)]
 
 
+class rve_request_result(C.Structure):
+    _fields_ = [("id", C.c_long), ("status", C.c_int), ("fractured", C.c_int), ("n_done", C.c_int),
+                ("toughness", C.c_double), ("E_last", C.c_double), ("Sigma_last", C.c_double),
+                ("T_last", C.c_double), ("Sigma_max", C.c_double), ("t_submit", C.c_double),
+                ("t_start", C.c_double), ("t_end", C.c_double), ("voxel_updates", C.c_long)]
+
+
 rve_handle = C.c_void_p
+rve_server = C.c_void_p
 _dp = C.POINTER(C.c_double)
 
 _SIGS = {
@@ -65,6 +73,14 @@ _SIGS = {
     "rve_launch_count": (C.c_long, [rve_handle]),
     "rve_destroy": (C.c_int, [rve_handle]),
     "rve_strerror": (C.c_char_p, [C.c_int]),
+    "rve_footprint_bytes": (C.c_size_t, [C.POINTER(rve_config)]),
+    "rve_server_create": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(rve_server)]),
+    "rve_server_submit": (C.c_int, [rve_server, C.c_long, C.POINTER(rve_config), C.POINTER(rve_micro), C.c_int,
+                                    C.c_double]),
+    "rve_server_wait": (C.c_int, [rve_server, C.POINTER(rve_request_result), C.c_int, C.c_double,
+                                  C.POINTER(C.c_int)]),
+    "rve_server_stats": (C.c_int, [rve_server, C.POINTER(C.c_int), C.POINTER(C.c_size_t), C.POINTER(C.c_long)]),
+    "rve_server_destroy": (C.c_int, [rve_server]),
     "rve_dissipation_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_double, C.c_int, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }

@@ -27,6 +27,30 @@ def _dptr(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+def make_micro(m):
+    """rve_micro for a synth.Microstructure-like object; returns (struct, arrays to keep alive)."""
+    keep = [np.ascontiguousarray(m.grain_id, np.int32).reshape(-1),
+            np.ascontiguousarray(m.C_cubic, np.float64).reshape(-1),
+            np.ascontiguousarray(m.R, np.float64).reshape(-1),
+            np.ascontiguousarray(m.Gc, np.float64).reshape(-1),
+            np.ascontiguousarray(m.cleave_n, np.float64).reshape(-1),
+            np.ascontiguousarray(m.beta, np.float64).reshape(-1)]
+    gid, Cc, R, Gc, cn, be = keep
+    mi = capi.rve_micro()
+    mi.grain_id = gid.ctypes.data_as(C.POINTER(C.c_int32))
+    mi.n_grains = int(m.C_cubic.shape[0])
+    mi.C_cubic, mi.R, mi.Gc, mi.cleave_n, mi.beta = _dptr(Cc), _dptr(R), _dptr(Gc), _dptr(cn), _dptr(be)
+    cr = m.crack
+    mi.crack_kind, mi.crack_row, mi.crack_x0, mi.crack_len = cr.kind, cr.row, cr.x0, cr.length
+    mi.crack_phi_M, mi.crack_stiffness = cr.phi_M, cr.stiffness
+    return mi, keep
+
+
+def workload_config(w, **kw):
+    m = w.micro
+    return make_config(m.dim, m.n, w.ell, w.k_res, w.split, 0 if w.precision == "fp64" else 1, f=w.f, **kw)
+
+
 class Rve:
     """One RVE resident on the GPU.
 
@@ -44,27 +68,12 @@ class Rve:
 
     @classmethod
     def from_workload(cls, w, **kw):
-        m = w.micro
-        cfg = make_config(m.dim, m.n, w.ell, w.k_res, w.split, 0 if w.precision == "fp64" else 1, f=w.f, **kw)
-        r = cls(cfg)
-        r.set_microstructure(m)
+        r = cls(workload_config(w, **kw))
+        r.set_microstructure(w.micro)
         return r
 
     def set_microstructure(self, m):
-        self._keep = [np.ascontiguousarray(m.grain_id, np.int32).reshape(-1),
-                      np.ascontiguousarray(m.C_cubic, np.float64).reshape(-1),
-                      np.ascontiguousarray(m.R, np.float64).reshape(-1),
-                      np.ascontiguousarray(m.Gc, np.float64).reshape(-1),
-                      np.ascontiguousarray(m.cleave_n, np.float64).reshape(-1),
-                      np.ascontiguousarray(m.beta, np.float64).reshape(-1)]
-        gid, Cc, R, Gc, cn, be = self._keep
-        mi = capi.rve_micro()
-        mi.grain_id = gid.ctypes.data_as(C.POINTER(C.c_int32))
-        mi.n_grains = int(m.C_cubic.shape[0])
-        mi.C_cubic, mi.R, mi.Gc, mi.cleave_n, mi.beta = _dptr(Cc), _dptr(R), _dptr(Gc), _dptr(cn), _dptr(be)
-        cr = m.crack
-        mi.crack_kind, mi.crack_row, mi.crack_x0, mi.crack_len = cr.kind, cr.row, cr.x0, cr.length
-        mi.crack_phi_M, mi.crack_stiffness = cr.phi_M, cr.stiffness
+        mi, self._keep = make_micro(m)
         capi.check(capi.lib().set_microstructure(self.h, C.byref(mi)), "set_microstructure")
 
     def step(self, dtau):

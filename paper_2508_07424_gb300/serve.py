@@ -1,0 +1,88 @@
+"""Serving helper over the library's request server (rve_server_*): marshalling and trace replay.
+
+The scheduling itself (admission by HBM footprint, worker threads, one stream per request) is
+native code in csrc/pff_serve.cu; this module submits requests at their arrival times and
+collects the results.
+"""
+import ctypes as C
+import math
+import threading
+import time
+
+from . import capi
+from .rve import make_micro, workload_config
+
+
+class Server:
+    def __init__(self, max_inflight=8, hbm_budget_bytes=64 << 30):
+        self.h = capi.rve_server()
+        capi.check(capi.lib().rve_server_create(max_inflight, hbm_budget_bytes, C.byref(self.h)), "rve_server_create")
+        self._keep = []
+
+    @staticmethod
+    def footprint(w, **kw):
+        cfg = workload_config(w, **kw)
+        return capi.lib().rve_footprint_bytes(C.byref(cfg))
+
+    def submit(self, rid, w, n_inc, dtau=None, **kw):
+        cfg = workload_config(w, **kw)
+        mi, keep = make_micro(w.micro)
+        rc = capi.lib().rve_server_submit(self.h, rid, C.byref(cfg), C.byref(mi), n_inc, dtau or w.dtau)
+        return rc
+
+    def wait(self, max_n=64, timeout=1.0):
+        buf = (capi.rve_request_result * max_n)()
+        n = C.c_int()
+        capi.check(capi.lib().rve_server_wait(self.h, buf, max_n, timeout, C.byref(n)), "rve_server_wait")
+        return [{k: getattr(buf[i], k) for k, _ in buf[i]._fields_} for i in range(n.value)]
+
+    def stats(self):
+        p, b, q = C.c_int(), C.c_size_t(), C.c_long()
+        capi.check(capi.lib().rve_server_stats(self.h, C.byref(p), C.byref(b), C.byref(q)), "rve_server_stats")
+        return {"peak_inflight": p.value, "peak_bytes": b.value, "pending": q.value}
+
+    def close(self):
+        if self.h:
+            capi.lib().rve_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return math.nan
+    k = (len(xs) - 1) * q
+    lo, hi = int(math.floor(k)), int(math.ceil(k))
+    return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
+
+
+def replay(server, requests, time_scale=1.0, **kw):
+    """requests: list of (arrival_s, workload, n_inc). Submits each at its (scaled) arrival time,
+    collects every result. Returns (results by id, wall seconds)."""
+    t0 = time.perf_counter()
+    out = {}
+    done = threading.Event()
+
+    def feeder():
+        for i, (ta, w, n_inc) in enumerate(requests):
+            delay = t0 + ta * time_scale - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            rc = server.submit(i, w, n_inc, **kw)
+            if rc != capi.RVE_OK:
+                out[i] = {"id": i, "status": rc}
+        done.set()
+
+    th = threading.Thread(target=feeder, daemon=True)
+    th.start()
+    while len(out) < len(requests):
+        for r in server.wait(64, 0.5):
+            out[r["id"]] = r
+    th.join()
+    return out, time.perf_counter() - t0

@@ -367,6 +367,28 @@ def build_request(kind, dims, n, seed, n_inc=100):
     return polycrystal_1024(n_inc=n_inc, seed=seed, n=n, n_grains=max(8, (200 * n * n) // (1024 * 1024)))
 
 
+def serving_mix(count=24, seed=4, n_inc=15, n_total=100, sizes2d=(64, 128, 256), sizes3d=(32,)):
+    """A seeded request mix for the serving path: half 2D / half 3D grids, fibre composites and
+    polycrystals from the generators above (fibre radius n/25.6, 50-200 grains). Each request
+    uses the dissipation increment of a ``n_total``-increment run (as the benchmark workloads do)
+    and is served for its first ``n_inc`` increments (or until fracture)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        is3d = rng.uniform() < 0.5
+        n = int(rng.choice(sizes3d if is3d else sizes2d))
+        s = seed * 100000 + i
+        if is3d:
+            w = polycrystal_3d(n, int(rng.integers(50, 201)), s, n_inc=n_total)
+        elif rng.uniform() < 0.5:
+            w = fibre_composite_512(n_inc=n_total, seed=s, n=n, radius=n / 25.6)
+        else:
+            w = polycrystal_1024(n_inc=n_total, seed=s, n=n, n_grains=int(rng.integers(50, 201)))
+        w.n_inc = n_inc
+        out.append(w)
+    return out
+
+
 def small_cases():
     """Small seeded cases for parity tests (several FFT tiles, non-square grids)."""
     cases = {}

@@ -1,0 +1,82 @@
+"""Serving path: concurrent RVE solves on one GPU through the native request server.
+
+* each result is the same alone and in the mix (the kernels of one RVE do not depend on what
+  else runs: same launch shapes, deterministic reductions), compared bit for bit;
+* admission honours the HBM budget (a budget that fits one request keeps one in flight);
+* a failing request is retired with its status and the others complete.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    from paper_2508_07424_gb300 import build, capi, serve
+    from paper_2508_07424_gb300.rve import Rve
+    build.build()
+    return capi, serve, Rve
+
+
+def _mix():
+    cases = synth.small_cases()
+    ws = [cases["homog32"], cases["fibre64x16"], cases["poly32"], cases["poly3d"],
+          synth.replace(cases["fibre64x16"], precision="fp32r"), synth.replace(cases["poly32"], precision="fp32r")]
+    return ws
+
+
+def _alone(Rve, w, n_inc):
+    g = Rve.from_workload(w, tol_stag=1e-9)
+    last = None
+    for _ in range(n_inc):
+        last = g.step(w.dtau)
+        if last["fractured"]:
+            break
+    return last
+
+
+def test_results_alone_equal_results_in_the_mix(mods):
+    capi, serve, Rve = mods
+    ws = _mix()
+    n_inc = 3
+    srv = serve.Server(max_inflight=len(ws), hbm_budget_bytes=64 << 30)
+    reqs = [(0.0, w, n_inc) for w in ws]
+    out, _ = serve.replay(srv, reqs, tol_stag=1e-9)
+    st = srv.stats()
+    srv.close()
+    assert st["peak_inflight"] >= 2
+    for i, w in enumerate(ws):
+        r = out[i]
+        assert r["status"] == capi.RVE_OK, r
+        a = _alone(Rve, w, n_inc)
+        assert r["n_done"] == a["n"]
+        assert r["E_last"] == a["E"] and r["Sigma_last"] == a["Sigma"] and r["T_last"] == a["T"], (i, r, a)
+
+
+def test_admission_respects_the_hbm_budget(mods):
+    capi, serve, Rve = mods
+    ws = _mix()[:4]
+    one = max(serve.Server.footprint(w) for w in ws)
+    srv = serve.Server(max_inflight=4, hbm_budget_bytes=int(one * 1.2))
+    out, _ = serve.replay(srv, [(0.0, w, 1) for w in ws])
+    st = srv.stats()
+    srv.close()
+    assert all(r["status"] == capi.RVE_OK for r in out.values())
+    assert st["peak_inflight"] == 1 and st["peak_bytes"] <= int(one * 1.2)
+
+
+def test_failing_request_is_retired_and_others_complete(mods):
+    capi, serve, Rve = mods
+    ws = _mix()[:3]
+    import copy
+    bad = copy.deepcopy(ws[0])
+    bad.micro.grain_id = bad.micro.grain_id.copy()
+    bad.micro.grain_id[0, 0, 0] = 99          # no such grain: set_microstructure rejects it
+    srv = serve.Server(max_inflight=2)
+    out, _ = serve.replay(srv, [(0.0, ws[1], 1), (0.0, bad, 1), (0.0, ws[2], 1)])
+    srv.close()
+    assert out[1]["status"] == capi.RVE_EINVAL
+    assert out[0]["status"] == capi.RVE_OK and out[2]["status"] == capi.RVE_OK
