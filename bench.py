@@ -153,7 +153,6 @@ def run_gpu(args):
     clocks = Clocks(local)
     clocks.start()
     launches0 = g.launches()
-    g.timing(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     vu = 0
     results = []
@@ -169,10 +168,16 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.barrier()
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    ax_ms, ax_n, ax_bytes = g.timing()
-    g.timing(False)
     launches = g.launches() - launches0
     clk = clocks.stop()
+    # dominant-kernel timing: CUDA events around every launch of the mechanics spectral pass on
+    # the library stream, over 3 increments that follow the timed region (event records cannot sit
+    # inside the replayed CUDA graphs, so these increments launch plainly).
+    g.timing(True)
+    for _ in range(3):
+        g.step(w.dtau)
+    ax_ms, ax_n, ax_bytes = g.timing()
+    g.timing(False)
     tot_ms = ms
     tot_vu = vu
     if world > 1:
@@ -222,12 +227,14 @@ def run_gpu(args):
     if args.precision == "fp64":
         peak = 152 * 2 * 2 * 2.07e9 / 1e12   # FP64: 2 DFMA/clk/SM (1.26 TFLOP/s), see the design doc
         roof = {"kernel": "k_axis (mechanics: FFT_y + projection + inverse FFT_y)", "bound": "alu",
+                "timing": "CUDA events per launch over 3 instrumented increments after the timed region",
                 "achieved": flops_l / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "frac": flops_l / avg_s / 1e12 / peak, "peak_source": "FP64 unit count x max SM clock",
                 "traffic": None, "avg_launch_us": avg_s * 1e6, "launches": ax_n}
     else:
         peak = pk["hbm_gbs"]
         roof = {"kernel": "k_axis (mechanics: FFT_y + projection + inverse FFT_y)", "bound": "hbm",
+                "timing": "CUDA events per launch over 3 instrumented increments after the timed region",
                 "achieved": bytes_l / avg_s / 1e9, "peak": peak, "unit": "GB/s",
                 "frac": bytes_l / avg_s / 1e9 / peak, "peak_source": src, "traffic": None,
                 "avg_launch_us": avg_s * 1e6, "launches": ax_n}
@@ -322,6 +329,12 @@ def serving(args):
     out, wall = serve.replay(srv, reqs)
     st = srv.stats()
     srv.close()
+    # capacity: the same requests all submitted at t = 0
+    srv = serve.Server(max_inflight=8, hbm_budget_bytes=int(0.5 * free))
+    out_sat, wall_sat = serve.replay(srv, [(0.0, w2, n) for (_, w2, n) in reqs])
+    st_sat = srv.stats()
+    srv.close()
+    ok_sat = [r for r in out_sat.values() if r["status"] == 0]
     ok = [r for r in out.values() if r["status"] == 0]
     lat = [r["t_end"] - r["t_submit"] for r in ok]
     return {"requests": len(ws), "increments_per_request": args.serve_inc,
@@ -332,6 +345,11 @@ def serving(args):
                         "name": ws[r["id"]].name} for r in out.values() if r["status"] != 0],
             "voxel_updates_per_s": sum(r["voxel_updates"] for r in ok) / wall,
             "peak_inflight": st["peak_inflight"], "slots": 8, "precision": "fp32r",
+            "saturated": {"solves_per_s": len(ok_sat) / wall_sat, "wall_s": wall_sat,
+                          "p50_s": serve.percentile([r["t_end"] - r["t_submit"] for r in ok_sat], 0.5),
+                          "p99_s": serve.percentile([r["t_end"] - r["t_submit"] for r in ok_sat], 0.99),
+                          "peak_inflight": st_sat["peak_inflight"],
+                          "what": "all requests submitted at t=0 (server capacity)"},
             "plain_fp64_one_by_one": {"solves_per_s": rate_plain, "p50_s": serve.percentile(lat_plain, 0.5),
                                       "p99_s": serve.percentile(lat_plain, 0.99),
                                       "service_p50_s": serve.percentile(serial, 0.5), "failed": plain_failed}}
@@ -411,8 +429,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=24)
-    ap.add_argument("--serve-inc", type=int, default=15)
+    ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--serve-inc", type=int, default=10)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     out = run_reference(args) if args.impl == "reference" else run_gpu(args)

@@ -21,6 +21,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/pff_rve.h"
@@ -611,6 +612,57 @@ struct Engine : EngineBase {
     double bytes_mech_axis = 0.0;
     std::map<const void *, size_t> smem_set;
     int cw_y = 2, cw_z = 2;
+    // CUDA graphs of one iteration chunk, keyed by (solver kind, solution buffer, coefficient
+    // pointer): the kernels of a chunk take only pointers and the device scalar block, so one
+    // captured graph is replayed for every chunk of every later solve of the same kind.
+    cudaStream_t cap_st = nullptr;
+    struct GraphEntry { cudaGraphExec_t exec; long nodes; };
+    std::map<std::tuple<int, const void *, const void *>, GraphEntry> graphs;
+    bool use_graphs = true;
+
+    // Run `body` (which launches one chunk on `st`) as a replay of a cached CUDA graph; the first
+    // call of a key launches plainly and the second captures. Falls back to plain launches while
+    // per-kernel timing is on (event records cannot sit inside a replayed graph).
+    template <class F> void run_chunk(int kind, const void *a, const void *b, F &&body) {
+        if (!use_graphs || timing) { body(); return; }
+        auto key = std::make_tuple(kind, a, b);
+        auto it = graphs.find(key);
+        if (it != graphs.end()) {
+            if (it->second.exec) {
+                CK(cudaGraphLaunch(it->second.exec, st));
+                launches += it->second.nodes;
+                return;
+            }
+            // second use: capture on the private stream, then replay on the handle's stream
+            if (!cap_st) CK(cudaStreamCreateWithFlags(&cap_st, cudaStreamNonBlocking));
+            cudaStream_t keep = st;
+            const long l0 = launches;
+            st = cap_st;
+            CK(cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal));
+            try {
+                body();
+            } catch (...) {
+                cudaGraph_t gtmp;
+                cudaStreamEndCapture(cap_st, &gtmp);
+                st = keep;
+                throw;
+            }
+            cudaGraph_t graph;
+            CK(cudaStreamEndCapture(cap_st, &graph));
+            st = keep;
+            cudaGraphExec_t exec;
+            CK(cudaGraphInstantiate(&exec, graph, 0));
+            CK(cudaGraphDestroy(graph));
+            it->second.exec = exec;
+            it->second.nodes = launches - l0;
+            launches = l0;
+            CK(cudaGraphLaunch(exec, st));
+            launches += it->second.nodes;
+            return;
+        }
+        graphs[key] = GraphEntry{nullptr, 0};
+        body();
+    }
 
     template <typename P> P *alloc(size_t n) {
         void *p = nullptr;
@@ -706,6 +758,11 @@ struct Engine : EngineBase {
     }
 
     void release() {
+        for (auto &kv : graphs)
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        graphs.clear();
+        if (cap_st) cudaStreamDestroy(cap_st);
+        cap_st = nullptr;
         for (auto &e : ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
         ev_pool.clear();
         for (void *p : allocs) cudaFree(p);
@@ -844,12 +901,14 @@ struct Engine : EngineBase {
                 x_inv<NSx>(EpiMechInit<T, NSx>{true, mr, N}, sc);
             }
             for (;;) {
-                for (int c = 0; c < chunk; ++c) {
-                    x_fwd<NSx>(dir, sc);
-                    spectral<NSx, NSx>(proj, sc, true);
-                    x_inv<NSx>(eq, sc);
-                    pointwise(up, sc);
-                }
+                run_chunk(1, phi_in, nullptr, [&] {
+                    for (int c = 0; c < chunk; ++c) {
+                        x_fwd<NSx>(dir, sc);
+                        spectral<NSx, NSx>(proj, sc, true);
+                        x_inv<NSx>(eq, sc);
+                        pointwise(up, sc);
+                    }
+                });
                 read_sc(sc);
                 if (h_sc->done) break;
             }
@@ -896,12 +955,14 @@ struct Engine : EngineBase {
             k_inner_tol<<<1, 1, 0, st>>>(sc, 1e-6);
             ++launches;
             for (;;) {
-                for (int c = 0; c < 8; ++c) {
-                    x_fwd<3>(dir, sc);
-                    spectral<3, 3>(proj, sc, true);
-                    x_inv<3>(eq, sc);
-                    pointwise(up, sc);
-                }
+                run_chunk(2, phi_in, nullptr, [&] {
+                    for (int c = 0; c < 8; ++c) {
+                        x_fwd<3>(dir, sc);
+                        spectral<3, 3>(proj, sc, true);
+                        x_inv<3>(eq, sc);
+                        pointwise(up, sc);
+                    }
+                });
                 read_sc(sc);
                 if (h_sc->done) break;
             }
@@ -946,16 +1007,18 @@ struct Engine : EngineBase {
             spectral<1, 1>(prec, sc);
             x_inv<1>(ez, sc);
             for (;;) {
-                for (int c = 0; c < chunk; ++c) {
-                    x_fwd<1>(pdir, sc);
-                    spectral<1, Dx>(grad, sc);
-                    x_mid<Dx>(flux, sc);
-                    spectral<Dx, 1>(divo, sc);
-                    x_inv<1>(eq, sc);
-                    x_fwd<1>(pu, sc);
-                    spectral<1, 1>(prec, sc);
-                    x_inv<1>(ez, sc);
-                }
+                run_chunk(3, x, co.Ktab, [&] {
+                    for (int c = 0; c < chunk; ++c) {
+                        x_fwd<1>(pdir, sc);
+                        spectral<1, Dx>(grad, sc);
+                        x_mid<Dx>(flux, sc);
+                        spectral<Dx, 1>(divo, sc);
+                        x_inv<1>(eq, sc);
+                        x_fwd<1>(pu, sc);
+                        spectral<1, 1>(prec, sc);
+                        x_inv<1>(ez, sc);
+                    }
+                });
                 read_sc(sc);
                 if (h_sc->done) break;
             }

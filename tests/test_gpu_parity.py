@@ -280,3 +280,18 @@ def test_homogeneous_plate_64_with_split_first_increment(cap):
     o = st.curve[-1]
     for k in ("E", "Sigma", "D", "T"):
         assert abs(r[k] - o[k]) <= 1e-9 * abs(o[k]), (k, r[k], o[k])
+
+
+def test_graph_replays_match_plain_launches(cap):
+    """Iteration chunks replayed from captured CUDA graphs give the same bits as plain launches
+    (per-kernel timing mode launches plainly)."""
+    from paper_2508_07424_gb300.rve import Rve
+    for name, prec in (("fibre64x16", "fp64"), ("poly3d", "fp32r")):
+        w = synth.replace(synth.small_cases()[name], precision=prec)
+        a = Rve.from_workload(w)
+        b = Rve.from_workload(w)
+        b.timing(True)
+        for _ in range(3):
+            ra, rb = a.step(w.dtau), b.step(w.dtau)
+            assert ra == rb
+        assert np.array_equal(a.get(cap.RVE_FIELD_PHI), b.get(cap.RVE_FIELD_PHI))
