@@ -133,6 +133,13 @@ __global__ void k_crack_setup(long long N, int nx, int ny, const int *gid0, int 
     phi_disc[v] = pd;
 }
 
+// Loop condition of a solve captured as a conditional (while) graph node: keep iterating while
+// the device scalars say the solve is not done. The solve always ends: the update kernels set
+// done at convergence, at the iteration cap, on breakdown and on a non-finite scalar.
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const Scal *sc) {
+    cudaGraphSetConditional(h, sc->done ? 0u : 1u);
+}
+
 __global__ void k_init_scal(Scal *sc, double tol2, int max_iters, double abar, double bbar) {
     sc->done = 0; sc->flag = 0; sc->iters = 0; sc->first = 1; sc->max_iters = max_iters;
     sc->tol2 = tol2; sc->beta = 0.0; sc->alpha = 0.0; sc->counter = 0u; sc->abar = abar; sc->bbar = bbar;
@@ -620,6 +627,70 @@ struct Engine : EngineBase {
     std::map<std::tuple<int, const void *, const void *>, GraphEntry> graphs;
     bool use_graphs = true;
 
+    // Whole iterative solves as one graph launch: a conditional while node whose body is one
+    // iteration plus k_loop_cond. Built once per key by capturing `body` into the node's body
+    // graph; returns false (caller falls back to chunks) when graphs are off or timing is on.
+    struct LoopEntry { cudaGraphExec_t exec; long body_nodes; bool failed; };
+    std::map<std::tuple<int, const void *, const void *>, LoopEntry> loops;
+    bool use_loops = true;
+    template <class F> bool run_loop(int kind, const void *a, const void *b, Scal *s, F &&body) {
+        if (!use_graphs || !use_loops || timing) return false;
+        auto key = std::make_tuple(kind, a, b);
+        auto it = loops.find(key);
+        if (it == loops.end()) {
+            LoopEntry e{nullptr, 0, false};
+            if (!cap_st) CK(cudaStreamCreateWithFlags(&cap_st, cudaStreamNonBlocking));
+            cudaGraph_t g = nullptr;
+            bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+            cudaGraphConditionalHandle h;
+            ok = ok && cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+            cudaGraphNode_t node;
+            alignas(cudaGraphNodeParams) unsigned char cpbuf[sizeof(cudaGraphNodeParams)];
+            std::memset(cpbuf, 0, sizeof(cpbuf));
+            cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cpbuf);
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            ok = ok && cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+            if (ok) {
+                cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+                cudaStream_t keep = st;
+                const long l0 = launches;
+                st = cap_st;
+                ok = cudaStreamBeginCaptureToGraph(cap_st, bodyg, nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                if (ok) {
+                    try {
+                        body();
+                        k_loop_cond<<<1, 1, 0, st>>>(h, s);
+                        ++launches;
+                    } catch (...) {
+                        ok = false;
+                    }
+                    cudaGraph_t out_g;
+                    ok = (cudaStreamEndCapture(cap_st, &out_g) == cudaSuccess) && ok;
+                }
+                st = keep;
+                e.body_nodes = launches - l0;
+                launches = l0;
+                ok = ok && cudaGraphInstantiate(&e.exec, g, 0) == cudaSuccess;
+            }
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();  // a refused construction is not an error of the solve
+            e.failed = !ok;
+            if (!ok) e.exec = nullptr;
+            it = loops.emplace(key, e).first;
+        }
+        if (it->second.failed) return false;
+        CK(cudaGraphLaunch(it->second.exec, st));
+        return true;
+    }
+    void count_loop(int kind, const void *a, const void *b, int iters) {
+        auto it = loops.find(std::make_tuple(kind, a, b));
+        if (it != loops.end() && !it->second.failed) launches += (long)std::max(1, iters) * it->second.body_nodes;
+    }
+
     // Run `body` (which launches one chunk on `st`) as a replay of a cached CUDA graph; the first
     // call of a key launches plainly and the second captures. Falls back to plain launches while
     // per-kernel timing is on (event records cannot sit inside a replayed graph).
@@ -758,6 +829,9 @@ struct Engine : EngineBase {
     }
 
     void release() {
+        for (auto &kv : loops)
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        loops.clear();
         for (auto &kv : graphs)
             if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
         graphs.clear();
@@ -900,17 +974,23 @@ struct Engine : EngineBase {
                 spectral<NSx, NSx>(proj, sc, true);
                 x_inv<NSx>(EpiMechInit<T, NSx>{true, mr, N}, sc);
             }
-            for (;;) {
-                run_chunk(1, phi_in, nullptr, [&] {
-                    for (int c = 0; c < chunk; ++c) {
-                        x_fwd<NSx>(dir, sc);
-                        spectral<NSx, NSx>(proj, sc, true);
-                        x_inv<NSx>(eq, sc);
-                        pointwise(up, sc);
-                    }
-                });
+            auto iter_body = [&] {
+                x_fwd<NSx>(dir, sc);
+                spectral<NSx, NSx>(proj, sc, true);
+                x_inv<NSx>(eq, sc);
+                pointwise(up, sc);
+            };
+            if (run_loop(1, phi_in, nullptr, sc, iter_body)) {
                 read_sc(sc);
-                if (h_sc->done) break;
+                count_loop(1, phi_in, nullptr, h_sc->iters);
+            } else {
+                for (;;) {
+                    run_chunk(1, phi_in, nullptr, [&] {
+                        for (int c = 0; c < chunk; ++c) iter_body();
+                    });
+                    read_sc(sc);
+                    if (h_sc->done) break;
+                }
             }
             iters += h_sc->iters;
             if (h_sc->flag) return RVE_EBREAKDOWN;
@@ -954,17 +1034,23 @@ struct Engine : EngineBase {
             pointwise(ek, sc);
             k_inner_tol<<<1, 1, 0, st>>>(sc, 1e-6);
             ++launches;
-            for (;;) {
-                run_chunk(2, phi_in, nullptr, [&] {
-                    for (int c = 0; c < 8; ++c) {
-                        x_fwd<3>(dir, sc);
-                        spectral<3, 3>(proj, sc, true);
-                        x_inv<3>(eq, sc);
-                        pointwise(up, sc);
-                    }
-                });
+            auto iter_body = [&] {
+                x_fwd<3>(dir, sc);
+                spectral<3, 3>(proj, sc, true);
+                x_inv<3>(eq, sc);
+                pointwise(up, sc);
+            };
+            if (run_loop(2, phi_in, nullptr, sc, iter_body)) {
                 read_sc(sc);
-                if (h_sc->done) break;
+                count_loop(2, phi_in, nullptr, h_sc->iters);
+            } else {
+                for (;;) {
+                    run_chunk(2, phi_in, nullptr, [&] {
+                        for (int c = 0; c < 8; ++c) iter_body();
+                    });
+                    read_sc(sc);
+                    if (h_sc->done) break;
+                }
             }
             iters += h_sc->iters;
             if (h_sc->flag) return RVE_EBREAKDOWN;
@@ -1006,21 +1092,27 @@ struct Engine : EngineBase {
             x_fwd<1>(ProField<T>{true, dr}, sc);
             spectral<1, 1>(prec, sc);
             x_inv<1>(ez, sc);
-            for (;;) {
-                run_chunk(3, x, co.Ktab, [&] {
-                    for (int c = 0; c < chunk; ++c) {
-                        x_fwd<1>(pdir, sc);
-                        spectral<1, Dx>(grad, sc);
-                        x_mid<Dx>(flux, sc);
-                        spectral<Dx, 1>(divo, sc);
-                        x_inv<1>(eq, sc);
-                        x_fwd<1>(pu, sc);
-                        spectral<1, 1>(prec, sc);
-                        x_inv<1>(ez, sc);
-                    }
-                });
+            auto iter_body = [&] {
+                x_fwd<1>(pdir, sc);
+                spectral<1, Dx>(grad, sc);
+                x_mid<Dx>(flux, sc);
+                spectral<Dx, 1>(divo, sc);
+                x_inv<1>(eq, sc);
+                x_fwd<1>(pu, sc);
+                spectral<1, 1>(prec, sc);
+                x_inv<1>(ez, sc);
+            };
+            if (run_loop(3, x, co.Ktab, sc, iter_body)) {
                 read_sc(sc);
-                if (h_sc->done) break;
+                count_loop(3, x, co.Ktab, h_sc->iters);
+            } else {
+                for (;;) {
+                    run_chunk(3, x, co.Ktab, [&] {
+                        for (int c = 0; c < chunk; ++c) iter_body();
+                    });
+                    read_sc(sc);
+                    if (h_sc->done) break;
+                }
             }
             iters += h_sc->iters;
             if (h_sc->flag) return RVE_EBREAKDOWN;
