@@ -29,10 +29,8 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 WORKLOAD = "fibre_composite_512"
 
 
-def workload_desc():
-    return ("512x512 plane-strain fibre composite, RSA discs r=20 at 30% voxel fraction, E_f/E_m=5, "
-            "Gc_f/Gc_m=2, nu=0.3, l=3, k=1e-6, central CTE crack 64 voxels (phi_M=0.8), "
-            "dtau=1.5*Gc*A_g/300, f=e_y(x)e_y")
+def workload_desc(name=WORKLOAD):
+    return WORKLOADS[name]
 
 
 def peaks():
@@ -103,9 +101,28 @@ def dist_env():
     return rank, world, local
 
 
-def make_workload(rank, precision):
+WORKLOADS = {
+    "fibre_composite_512": "512x512 plane-strain fibre composite, RSA discs r=20 at 30% voxel fraction, E_f/E_m=5, "
+                           "Gc_f/Gc_m=2, nu=0.3, l=3, k=1e-6, central CTE crack 64 voxels (phi_M=0.8), "
+                           "dtau=1.5*Gc*A_g/300, f=e_y(x)e_y",
+    "homogeneous_plate_64": "64x64 plane-strain homogeneous plate, E=1, nu=0.3, Gc=1, l=2, spectral split, CTE crack "
+                            "16 voxels at mid-height, dtau=1.5*Gc*A_g/100",
+    "polycrystal_1024": "1024x1024 periodic Voronoi polycrystal, 200 grains, cubic C11=1 C12=0.6 C44=0.5 (Zener 2.5), "
+                        "uniform in-plane orientations, cleavage beta=2, l=2, CTE crack 102 voxels, dtau=1.5*A_g/400",
+    "batched_3d_polycrystals": "16 periodic Voronoi 3D polycrystals, grids drawn from {32,64,128}^3, 50-200 grains, "
+                               "cubic C11=1 C12=0.6 C44=0.5 with SO(3)-uniform orientations, lognormal Gc (sigma 0.3), "
+                               "l=2, through CTE crack 0.1 n, dtau=1.5*<Gc>*A_g/100; run as 16 concurrent streams",
+}
+
+
+def make_workload(rank, precision, name=WORKLOAD):
     import synth
-    w = synth.fibre_composite_512(seed=1 + rank)
+    if name == "homogeneous_plate_64":
+        w = synth.homogeneous_plate_64()
+    elif name == "polycrystal_1024":
+        w = synth.polycrystal_1024(seed=2 + rank)
+    else:
+        w = synth.fibre_composite_512(seed=1 + rank)
     w.precision = precision
     return w
 
@@ -139,7 +156,9 @@ def run_gpu(args):
     from paper_2508_07424_gb300.rve import Rve
     build.build()
     stream = torch.cuda.current_stream()
-    w = make_workload(rank, args.precision)
+    if args.workload == "batched_3d_polycrystals":
+        return run_batched_3d(args, torch, stream)
+    w = make_workload(rank, args.precision, args.workload)
     tol = solver_tols(args.precision)
     g = Rve.from_workload(w, stream=stream.cuda_stream, **tol)
     N = g.nvox
@@ -223,6 +242,8 @@ def run_gpu(args):
     pk, src = peaks()
     word = 8 if args.precision == "fp64" else 4
     bytes_l, flops_l = axis_kernel_model(w.micro.n[0], w.micro.n[1], 3, word)
+    if w.micro.dim == 3:
+        bytes_l, flops_l = float("nan"), float("nan")
     avg_s = ax_ms * 1e-3 / max(ax_n, 1)
     if args.precision == "fp64":
         peak = 152 * 2 * 2 * 2.07e9 / 1e12   # FP64: 2 DFMA/clk/SM (1.26 TFLOP/s), see the design doc
@@ -239,7 +260,7 @@ def run_gpu(args):
                 "frac": bytes_l / avg_s / 1e9 / peak, "peak_source": src, "traffic": None,
                 "avg_launch_us": avg_s * 1e6, "launches": ax_n}
     out = {
-        "metric": "FFT-PFF voxel-updates/s (fibre composite 512^2 increments)",
+        "metric": f"FFT-PFF voxel-updates/s ({args.workload} increments)",
         "value": tot_vu / (tot_ms * 1e-3),
         "unit": "voxel-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -247,7 +268,7 @@ def run_gpu(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "desc": workload_desc(), "precision": args.precision,
+        "config": {"workload": args.workload, "desc": workload_desc(args.workload), "precision": args.precision,
                    "step": "one dissipation increment", "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas{world}"},
         "increments": [{k: r[k] for k in ("n", "mech_iters", "dmg_iters", "stag_iters", "root_evals")} for r in results],
@@ -256,13 +277,93 @@ def run_gpu(args):
         "roofline": roof,
         "e2e": e2e,
     }
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and args.workload == WORKLOAD:
         out["cpu_baseline"] = cpu_baseline(args, timed_steps=1)
-    if args.precision == "fp32r" and world == 1:
+    if args.precision == "fp32r" and world == 1 and args.workload == WORKLOAD:
         out["fp64_side_by_side"] = side_by_side_fp64(args, stream)
-    if not args.no_serve and world == 1:
+    if args.workload == "homogeneous_plate_64" and world == 1:
+        out["toughness_run"] = toughness_run(args, stream)
+    if not args.no_serve and world == 1 and args.workload == WORKLOAD:
         out["serving"] = serving(args)
     return out
+
+
+def toughness_run(args, stream):
+    """The 64^2 plate broken through: increments until the fracture point, G of Eq. (JaviGc)."""
+    from paper_2508_07424_gb300.rve import Rve
+    w = make_workload(0, args.precision, "homogeneous_plate_64")
+    g = Rve.from_workload(w, stream=stream.cuda_stream, **solver_tols(args.precision))
+    t0 = time.perf_counter()
+    n = 0
+    for _ in range(300):
+        r = g.step(w.dtau)
+        n = r["n"]
+        if r["fractured"]:
+            break
+    dt = time.perf_counter() - t0
+    out = {"increments": n, "fractured": bool(r["fractured"]), "wall_s": dt}
+    if r["fractured"]:
+        out["G_eff"] = g.toughness()
+        out["G_eff_over_Gc"] = out["G_eff"] / 1.0
+    g.close()
+    return out
+
+
+def run_batched_3d(args, torch, stream):
+    """16 3D polycrystal RVEs (grids 32^3..128^3), each on its own handle and stream, driven by
+    one host thread each; W untimed increments, then K timed increments of all RVEs."""
+    import threading
+
+    import synth
+    from paper_2508_07424_gb300.rve import Rve
+    ws = synth.batched_3d_polycrystals()
+    for w in ws:
+        w.precision = args.precision
+    tol = solver_tols(args.precision)
+    gs = [Rve.from_workload(w, **tol) for w in ws]
+
+    def drive(i, k, res):
+        vu = 0
+        for _ in range(k):
+            r = gs[i].step(ws[i].dtau)
+            vu += (r["mech_iters"] + r["dmg_iters"]) * gs[i].nvox
+        res[i] = vu
+
+    def run_all(k):
+        res = [0] * len(gs)
+        th = [threading.Thread(target=drive, args=(i, k, res)) for i in range(len(gs))]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        return sum(res)
+
+    run_all(args.warmup)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    l0 = sum(g.launches() for g in gs)
+    t0 = time.perf_counter()
+    vu = run_all(args.steps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    clk = clocks.stop()
+    launches = sum(g.launches() for g in gs) - l0
+    sizes = {}
+    for w in ws:
+        sizes[w.micro.n[0]] = sizes.get(w.micro.n[0], 0) + 1
+    for g in gs:
+        g.close()
+    return {"metric": "FFT-PFF voxel-updates/s (batched_3d_polycrystals increments)", "value": vu / dt,
+            "unit": "voxel-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32r" else "f64", "data": "synthetic",
+            "config": {"workload": "batched_3d_polycrystals", "desc": WORKLOADS["batched_3d_polycrystals"],
+                       "precision": args.precision, "grids": {f"{k}^3": v for k, v in sorted(sizes.items())},
+                       "step": "one dissipation increment of each of the 16 RVEs",
+                       "l2": "inputs larger than L2 (the 128^3 RVEs alone hold > 1 GB)"},
+            "gpu_launches": int(launches), "clocks": clk, "timing": "host wall clock with device synchronize",
+            "roofline": None, "e2e": None}
 
 
 def side_by_side_fp64(args, stream):
@@ -424,15 +525,19 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="fp32r", choices=["fp64", "fp32r"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32r"],
+                    help="default: fp64 for homogeneous_plate_64 (the parity configuration), fp32r otherwise")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=list(WORKLOADS))
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-inc", type=int, default=10)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.precision is None:
+        args.precision = "fp64" if args.workload == "homogeneous_plate_64" else "fp32r"
     out = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if out is not None:
         print(json.dumps(out))

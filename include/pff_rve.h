@@ -110,7 +110,14 @@ typedef struct {
     int mech_iters, dmg_iters, root_evals, stag_iters;
     int fractured;      /* 1 once Sigma^n <= fracture_ratio * max Sigma */
     double stag_err;    /* final staggered error of Eq. (errors_crack) */
+    int flags;          /* RVE_STEP_STAGNATED: accepted at the staggered noise floor (no improvement
+                           for 20 iterations, error within 100 x tol_stag); RVE_STEP_CUTBACK: the
+                           staggered iteration failed and the increment was split into halves
+                           (up to 4 levels), each committed as its own load-curve point; the
+                           iteration counts then cover every attempt */
 } rve_step_result;
+
+enum { RVE_STEP_STAGNATED = 1, RVE_STEP_CUTBACK = 2 };
 
 /* Committed scalar state (for checkpoints and state injection in tests). */
 typedef struct {
@@ -132,7 +139,8 @@ int rve_create(const rve_config *cfg, rve_handle *out);
  * Errors: RVE_EINVAL (ids out of range, split with a non-isotropic grain), RVE_ECUDA. */
 int set_microstructure(rve_handle h, const rve_micro *m);
 
-/* One increment at constant dissipation rate: tau^n = tau^{n-1} + dtau, then the staggered
+/* One increment at constant dissipation rate (with cutback, see rve_step_result.flags):
+ * tau^n = tau^{n-1} + dtau, then the staggered
  * solve of Eq. (SystemDisany) -- Fourier-Galerkin CG equilibrium at unit load, the smallest
  * E >= 0 with D(phi(E)) = tau^n, FFT-preconditioned CG for phi -- until the stopping test of
  * Eq. (errors_crack); then the history update, Sigma, E_mec and the trapezoid T^n (Eq. (ABC)).
@@ -175,6 +183,8 @@ int rve_timing_get(rve_handle h, int kind, double *total_ms, long *launches, dou
 long rve_launch_count(rve_handle h);
 
 int rve_destroy(rve_handle h);
+/* Message of a status; for RVE_ENOCONV, RVE_ENOROOT, RVE_EBREAKDOWN and RVE_ECUDA it is the
+ * last failure recorded on the calling thread (which stage failed, with its numbers). */
 const char *rve_strerror(int status);
 
 /* ---- serving: many RVE toughness solves on one GPU --------------------------------------------

@@ -56,7 +56,7 @@ class Params:
     max_mech: int = 20000
     max_dmg: int = 20000
     max_root: int = 200
-    max_stag: int = 2000
+    max_stag: int = 300
     fracture_ratio: float = 0.01
 
 
@@ -402,6 +402,8 @@ def increment(model, st, dtau, anderson_m=5):
     E = st.E
     stats = {"mech_iters": 0, "dmg_iters": 0, "root_evals": 0, "stag_iters": 0}
     X, Gv = [], []
+    best, k_best = math.inf, 0
+    stats["stagnated"] = False
     for k in range(p.max_stag):
         F1, it = mech_solve(model, phi, F1)
         stats["mech_iters"] += it
@@ -416,6 +418,15 @@ def increment(model, st, dtau, anderson_m=5):
         stats["stag_iters"] = k + 1
         if err < p.tol_stag:
             phi = phi_new
+            break
+        # noise floor: accept when the error has not improved for 20 iterations and is within
+        # 100 x tol (the conditioning of cracked voxels, k << 1, bounds how far the staggered
+        # error can fall in floating point)
+        if err < best:
+            best, k_best = err, k
+        if k - k_best >= 20 and err <= 100.0 * p.tol_stag:
+            phi = phi_new
+            stats["stagnated"] = True
             break
         if anderson_m > 0:
             X.append(phi)
@@ -454,13 +465,28 @@ def params_from_workload(w, **kw):
     return Params(ell=w.ell, k_res=w.k_res, split=w.split, f6=tuple(w.f), **kw)
 
 
+def increment_with_cutback(model, st, dtau, depth=0):
+    """One increment; if the staggered iteration does not converge, two increments of half the
+    dissipation instead (recursively, up to four levels), each its own point of the load curve."""
+    try:
+        return increment(model, st, dtau)
+    except RuntimeError as e:
+        if "staggered" not in str(e) or depth >= 4:
+            raise
+    st1, s1 = increment_with_cutback(model, st, 0.5 * dtau, depth + 1)
+    if st1.fractured:
+        return st1, s1
+    st2, s2 = increment_with_cutback(model, st1, 0.5 * dtau, depth + 1)
+    return st2, {k: s1.get(k, 0) + s2.get(k, 0) for k in s2 if k != "stagnated"}
+
+
 def run(w, n_inc=None, params=None, stop_at_fracture=True, callback=None):
     """Full toughness run of a synth.Workload: returns (model, final state, G or None)."""
     p = params or params_from_workload(w)
     model = Model(w.micro, p)
     st = init_state(model)
     for _ in range(n_inc or w.n_inc):
-        st, _ = increment(model, st, w.dtau)
+        st, _ = increment_with_cutback(model, st, w.dtau)
         if callback:
             callback(model, st)
         if st.fractured and stop_at_fracture:

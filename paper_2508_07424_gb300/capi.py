@@ -7,6 +7,7 @@ from .build import LIB
 RVE_OK, RVE_EINVAL, RVE_ENOMEM, RVE_ESTATE, RVE_ENOCONV = 0, -1, -2, -3, -4
 RVE_ENOROOT, RVE_ETIMEOUT, RVE_ENOTFRACTURED, RVE_ECUDA, RVE_EBREAKDOWN = -5, -6, -7, -8, -9
 RVE_SPLIT_NONE, RVE_SPLIT_SPECTRAL = 0, 1
+RVE_STEP_STAGNATED, RVE_STEP_CUTBACK = 1, 2
 RVE_FP64, RVE_FP32R = 0, 1
 RVE_CRACK_NONE, RVE_CRACK_CTE, RVE_CRACK_CPFE = 0, 1, 2
 (RVE_FIELD_PHI, RVE_FIELD_H, RVE_FIELD_PSI_INI, RVE_FIELD_EPS, RVE_FIELD_SIGMA, RVE_FIELD_FLUCT1,
@@ -34,7 +35,7 @@ class rve_step_result(C.Structure):
     _fields_ = [("n", C.c_int), ("E", C.c_double), ("Sigma", C.c_double), ("D", C.c_double),
                 ("Emec", C.c_double), ("T", C.c_double), ("Gamma", C.c_double), ("tau", C.c_double),
                 ("mech_iters", C.c_int), ("dmg_iters", C.c_int), ("root_evals", C.c_int),
-                ("stag_iters", C.c_int), ("fractured", C.c_int), ("stag_err", C.c_double)]
+                ("stag_iters", C.c_int), ("fractured", C.c_int), ("stag_err", C.c_double), ("flags", C.c_int)]
 
 
 class rve_scalars(C.Structure):

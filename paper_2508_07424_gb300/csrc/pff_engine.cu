@@ -850,6 +850,10 @@ struct Engine : EngineBase {
     XiTab<T> xitab() const { return XiTab<T>{xi_x, xi_y, xi_z}; }
 
     // ---- launch helpers --------------------------------------------------------------------
+    static int fail(int code, const char *what) {
+        g_last_error = what;
+        return code;
+    }
     template <typename K> void prep_smem(K kernel, size_t bytes) {
         const void *key = (const void *)kernel;
         auto it = smem_set.find(key);
@@ -993,8 +997,8 @@ struct Engine : EngineBase {
                 }
             }
             iters += h_sc->iters;
-            if (h_sc->flag) return RVE_EBREAKDOWN;
-            if (!(h_sc->rr <= h_sc->tol2 * h_sc->scale2)) return RVE_ENOCONV;
+            if (h_sc->flag) return fail(RVE_EBREAKDOWN, "equilibrium CG: breakdown or non-finite scalar");
+            if (!(h_sc->rr <= h_sc->tol2 * h_sc->scale2)) return fail(RVE_ENOCONV, "equilibrium CG: iteration cap");
             if (!kSingle || h_sc->iters == 0) break;
         }
         PwPsi1<T, NSx> ps{false, Cm, mx, gid, psi1, {}, N};
@@ -1053,9 +1057,9 @@ struct Engine : EngineBase {
                 }
             }
             iters += h_sc->iters;
-            if (h_sc->flag) return RVE_EBREAKDOWN;
-            if (iters >= cfg.max_mech_iters) return RVE_ENOCONV;
-            if (newton == 99) return RVE_ENOCONV;
+            if (h_sc->flag) return fail(RVE_EBREAKDOWN, "split equilibrium: breakdown or non-finite scalar");
+            if (iters >= cfg.max_mech_iters) return fail(RVE_ENOCONV, "split equilibrium: CG iteration cap");
+            if (newton == 99) return fail(RVE_ENOCONV, "split equilibrium: Newton did not converge in 100 steps");
         }
         PwPsi1Split<T> ps{false, mx, lamT, muT, gid, psi1, {}, N};
         for (int a = 0; a < 3; ++a) ps.f[a] = (T)fM[a];
@@ -1115,8 +1119,8 @@ struct Engine : EngineBase {
                 }
             }
             iters += h_sc->iters;
-            if (h_sc->flag) return RVE_EBREAKDOWN;
-            if (!(h_sc->rr <= h_sc->tol2 * h_sc->scale2)) return RVE_ENOCONV;
+            if (h_sc->flag) return fail(RVE_EBREAKDOWN, "damage CG: breakdown or non-finite scalar");
+            if (!(h_sc->rr <= h_sc->tol2 * h_sc->scale2)) return fail(RVE_ENOCONV, "damage CG: iteration cap");
             if (!kSingle || h_sc->iters == 0) break;
         }
         return RVE_OK;
@@ -1315,7 +1319,7 @@ struct Engine : EngineBase {
             lo = E0; flo = f0; hi = lo + h;
             if ((rc = evaluate(hi, fhi))) return rc;
             while (fhi <= 0.0) {
-                if (++guard > 200) return RVE_ENOROOT;
+                if (++guard > 200) return fail(RVE_ENOROOT, "control: bracket search failed");
                 lo = hi; flo = fhi; h *= 4.0; hi = lo + h;
                 if ((rc = evaluate(hi, fhi))) return rc;
             }
@@ -1324,7 +1328,7 @@ struct Engine : EngineBase {
             if ((rc = evaluate(lo, flo))) return rc;
             while (flo >= 0.0) {
                 if (lo == 0.0) { E_out = 0.0; return RVE_OK; }
-                if (++guard > 200) return RVE_ENOROOT;
+                if (++guard > 200) return fail(RVE_ENOROOT, "control: bracket search (downward) failed");
                 hi = lo; fhi = flo; h *= 4.0; lo = std::max(0.0, hi - h);
                 if ((rc = evaluate(lo, flo))) return rc;
             }
@@ -1345,10 +1349,41 @@ struct Engine : EngineBase {
                 side = -1;
             }
         }
-        return RVE_ENOROOT;
+        return fail(RVE_ENOROOT, "control: no root of D(phi(E)) = tau within the evaluation cap");
     }
     // ---- one increment (a1-a11) ----------------------------------------------------------------
-    int step(double dtau, rve_step_result *out) override {
+    // One increment with cutback: when the staggered iteration does not converge (snap-back near
+    // coalescence), the increment is replaced by two of half the dissipation, recursively up to
+    // four levels; each sub-increment is committed as its own point of the load curve.
+    bool stag_failed = false;
+    int step(double dtau, rve_step_result *out) override { return step_cut(dtau, out, 0); }
+    int step_cut(double dtau, rve_step_result *out, int depth) {
+        rve_step_result a{};
+        int rc = step_once(dtau, &a);
+        if (rc == RVE_ENOCONV && stag_failed && depth < 4) {
+            rve_step_result b{}, c{};
+            rc = step_cut(0.5 * dtau, &b, depth + 1);
+            if (rc) return rc;
+            if (!b.fractured) {
+                rc = step_cut(0.5 * dtau, &c, depth + 1);
+                if (rc) return rc;
+            } else {
+                c = b;
+                std::memset(&b, 0, sizeof(b));
+            }
+            c.mech_iters += b.mech_iters + a.mech_iters;
+            c.dmg_iters += b.dmg_iters + a.dmg_iters;
+            c.root_evals += b.root_evals + a.root_evals;
+            c.stag_iters += b.stag_iters + a.stag_iters;
+            c.flags |= b.flags | RVE_STEP_CUTBACK;
+            if (out) *out = c;
+            return RVE_OK;
+        }
+        if (out) *out = a;
+        return rc;
+    }
+    int step_once(double dtau, rve_step_result *out) {
+        stag_failed = false;
         if (!micro_set) return RVE_ESTATE;
         rve_step_result r{};
         const double tau = S.tau + dtau;
@@ -1360,6 +1395,8 @@ struct Engine : EngineBase {
         std::deque<int> hist;  // slots of (X, G) in chronological order
         int next_slot = 0;
         bool converged = false;
+        double best = 1e300;
+        int k_best = 0;
         for (int k = 0; k < cfg.max_stag_iters; ++k) {
             int it = 0;
             int rc = mech_solve(phi_cur, it);
@@ -1386,6 +1423,13 @@ struct Engine : EngineBase {
             err = std::max(std::max(e1, e2), std::fabs(Dv - tau) / tau);
             r.stag_iters = k + 1;
             if (err < cfg.tol_stag) { converged = true; break; }
+            // noise floor: the error has not improved for 20 iterations and is within 100 x tol
+            if (err < best) { best = err; k_best = k; }
+            if (k - k_best >= 20 && err <= 100.0 * cfg.tol_stag) {
+                converged = true;
+                r.flags |= RVE_STEP_STAGNATED;
+                break;
+            }
             if (m > 0) {
                 // record (X = phi_cur, G = phi_trial), keep the last m + 1
                 int slot;
@@ -1425,7 +1469,15 @@ struct Engine : EngineBase {
                 CK(cudaMemcpyAsync(phi_cur, phi_trial, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
             }
         }
-        if (!converged) return RVE_ENOCONV;
+        if (!converged) {
+            stag_failed = true;
+            if (out) *out = r;
+            char buf[160];
+            std::snprintf(buf, sizeof(buf), "staggered iteration: %d iterations, error %.3e (tol %.1e) at increment %d",
+                          cfg.max_stag_iters, err, cfg.tol_stag, S.n + 1);
+            g_last_error = buf;
+            return RVE_ENOCONV;
+        }
         // commit (a8, a11): phi, H, strain, Sigma, E_mec, T
         CK(cudaMemcpyAsync(phi, phi_trial, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(H, Hcur, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
@@ -1628,7 +1680,7 @@ void rve_config_default(rve_config *c) {
     c->max_mech_iters = 20000;
     c->max_dmg_iters = 20000;
     c->max_root_evals = 200;
-    c->max_stag_iters = 2000;
+    c->max_stag_iters = 300;
     c->anderson_m = 5;
     c->fracture_ratio = 0.01;
     c->stream = nullptr;
@@ -1825,12 +1877,12 @@ const char *rve_strerror(int s) {
     case RVE_EINVAL: return "invalid argument";
     case RVE_ENOMEM: return "device allocation failed";
     case RVE_ESTATE: return "call out of order";
-    case RVE_ENOCONV: return "iteration did not converge";
-    case RVE_ENOROOT: return "dissipation constraint could not be bracketed";
+    case RVE_ENOCONV: return g_last_error.empty() ? "iteration did not converge" : g_last_error.c_str();
+    case RVE_ENOROOT: return g_last_error.empty() ? "dissipation constraint could not be bracketed" : g_last_error.c_str();
     case RVE_ETIMEOUT: return "device wait timed out";
     case RVE_ENOTFRACTURED: return "fracture point not reached";
     case RVE_ECUDA: return g_last_error.empty() ? "CUDA error" : g_last_error.c_str();
-    case RVE_EBREAKDOWN: return "CG breakdown or non-finite value";
+    case RVE_EBREAKDOWN: return g_last_error.empty() ? "CG breakdown or non-finite value" : g_last_error.c_str();
     default: return "unknown status";
     }
 }
