@@ -74,7 +74,8 @@ typedef struct {
     double tol_mech;       /* equilibrium: |P[sigma]| <= tol_mech |g C : f| */
     double tol_dmg;        /* damage CG: |r| <= tol_dmg |2H| */
     double tol_root;       /* control: |D - tau| <= tol_root tau */
-    double tol_stag;       /* staggered fixed point: the three ratios of Eq. (errors_crack) */
+    double tol_stag;       /* staggered fixed point: the three ratios of Eq. (errors_crack), the strain
+                              change measured in the degraded energy norm sqrt(sum d : g C : d) */
     int max_mech_iters, max_dmg_iters, max_root_evals, max_stag_iters;
     int anderson_m;        /* Anderson memory of the staggered iteration (0 = plain) */
     double fracture_ratio; /* fracture point F: Sigma^F <= ratio * max Sigma (Sec. 4.2) */
@@ -114,10 +115,12 @@ typedef struct {
                            for 20 iterations, error within 100 x tol_stag); RVE_STEP_CUTBACK: the
                            staggered iteration failed and the increment was split into halves
                            (up to 4 levels), each committed as its own load-curve point; the
-                           iteration counts then cover every attempt */
+                           iteration counts then cover every attempt; RVE_STEP_UNCONVERGED: even
+                           the deepest split did not converge and its last staggered iterate was
+                           kept (the increment is still a point of D = tau^n) */
 } rve_step_result;
 
-enum { RVE_STEP_STAGNATED = 1, RVE_STEP_CUTBACK = 2 };
+enum { RVE_STEP_STAGNATED = 1, RVE_STEP_CUTBACK = 2, RVE_STEP_UNCONVERGED = 4 };
 
 /* Committed scalar state (for checkpoints and state injection in tests). */
 typedef struct {

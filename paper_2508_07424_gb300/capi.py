@@ -7,7 +7,7 @@ from .build import LIB
 RVE_OK, RVE_EINVAL, RVE_ENOMEM, RVE_ESTATE, RVE_ENOCONV = 0, -1, -2, -3, -4
 RVE_ENOROOT, RVE_ETIMEOUT, RVE_ENOTFRACTURED, RVE_ECUDA, RVE_EBREAKDOWN = -5, -6, -7, -8, -9
 RVE_SPLIT_NONE, RVE_SPLIT_SPECTRAL = 0, 1
-RVE_STEP_STAGNATED, RVE_STEP_CUTBACK = 1, 2
+RVE_STEP_STAGNATED, RVE_STEP_CUTBACK, RVE_STEP_UNCONVERGED = 1, 2, 4
 RVE_FP64, RVE_FP32R = 0, 1
 RVE_CRACK_NONE, RVE_CRACK_CTE, RVE_CRACK_CPFE = 0, 1, 2
 (RVE_FIELD_PHI, RVE_FIELD_H, RVE_FIELD_PSI_INI, RVE_FIELD_EPS, RVE_FIELD_SIGMA, RVE_FIELD_FLUCT1,
