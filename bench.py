@@ -145,6 +145,20 @@ def axis_kernel_model(nx, ny, ns, word):
     return bytes_, flops
 
 
+def aggregate_over_ranks(ms, vu, world, device):
+    """Job-wide timing of replicas: the slowest rank's time (MAX) and all ranks' voxel-updates
+    (SUM). No data-path collective: each rank solves its own RVE."""
+    if world <= 1:
+        return ms, vu
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms), float(vu)], device=device, dtype=torch.float64)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0].item()), float(t[1].item())
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -197,16 +211,7 @@ def run_gpu(args):
         g.step(w.dtau)
     ax_ms, ax_n, ax_bytes = g.timing()
     g.timing(False)
-    tot_ms = ms
-    tot_vu = vu
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-        v = torch.tensor([float(vu)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(v, op=dist.ReduceOp.SUM)
-        tot_vu = float(v.item())
+    tot_ms, tot_vu = aggregate_over_ranks(ms, vu, world, "cuda")
 
     # e2e: the public C ABI from host buffers; every step uploads the microstructure, builds the
     # enriched crack, runs one increment and reads back the result and the damage field.

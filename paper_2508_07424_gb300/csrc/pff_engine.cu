@@ -906,11 +906,12 @@ struct Engine : EngineBase {
         CK(cudaGetLastError());
         ++launches;
     }
-    template <int NC, class Mid> void x_mid(const Mid &mid, Scal *s) {
+    template <int NC, class Mid> void x_mid(const Mid &mid, Scal *s) { x_mid2<NC, NC>(mid, s); }
+    template <int NCI, int NCO, class Mid> void x_mid2(const Mid &mid, Scal *s) {
         int th, bl; size_t sm; xcfg(th, bl, sm);
-        auto k = k_x_mid<T, NC, Mid>;
-        prep_smem(k, sm * NC);
-        k<<<bl, th, sm * NC, st>>>(g, spec, mid, tw[g.nx], s);
+        auto k = k_x_mid<T, NCI, NCO, Mid>;
+        prep_smem(k, sm * NCI);
+        k<<<bl, th, sm * NCI, st>>>(g, spec, mid, tw[g.nx], s);
         CK(cudaGetLastError());
         ++launches;
     }
@@ -978,11 +979,11 @@ struct Engine : EngineBase {
         x_fwd<NSx>(pro, sc);
         spectral<NSx, NSx>(proj, sc, true);
         x_inv<NSx>(EpiMechInit<T, NSx>{true, mr, N}, sc);
-        ProCGDir<T, NSx> dir;
+        if (!mw) mw = alloc<T>((size_t)NS * N);
+        ProCGCG<T, NSx> dir;
         (MechBase<T, NSx> &)dir = mb;
-        dir.r = mr; dir.p = mp; dir.scr = sc;
-        EpiMechQ<T, NSx> eq{true, mq, mp, N};
-        PwMechUpdate<T, NSx> up{true, mx, mr, mp, mq, sc, N};
+        dir.x = mx; dir.r = mr; dir.p = mp; dir.s = mq; dir.w = mw; dir.scr = sc;
+        EpiCGCG<T, NSx> eq{true, mw, mr, N};
         // FP64: one CG pass (as the oracle). FP32: iterative refinement -- each pass restarts CG
         // from the equilibrium residual recomputed from the current strain, until that true
         // residual meets the tolerance (a pass that needs no iteration).
@@ -1000,7 +1001,6 @@ struct Engine : EngineBase {
                 x_fwd<NSx>(dir, sc);
                 spectral<NSx, NSx>(proj, sc, true);
                 x_inv<NSx>(eq, sc);
-                pointwise(up, sc);
             };
             if (run_loop(1, phi_in, nullptr, sc, iter_body)) {
                 read_sc(sc);
@@ -1033,7 +1033,7 @@ struct Engine : EngineBase {
     // the tangent P[K(eps_k) : dx] = -P[sigma(eps_k)] to 1e-3 of its initial residual; stops when
     // |P[sigma]| <= tol_mech |sigma|. The problem is positively homogeneous of degree one, so the
     // unit-load solution scales with E >= 0.
-    T *epsk = nullptr;
+    T *epsk = nullptr, *mw = nullptr, *dw = nullptr;
     int mech_solve_split(const T *phi_in, int &iters) {
         if (!epsk) epsk = alloc<T>((size_t)3 * N);
         ProSplitStress<T> pst{true, mx, phi_in, lamT, muT, gid, (T)cfg.k_res, {}, N};
@@ -1092,37 +1092,30 @@ struct Engine : EngineBase {
         ProDmgInit<T> pi{true, mode, E, psi1, psi_ini, H, Hcur, rhs, x, amean, bbar, (double)co.hmul, N};
         OpGrad<C, Dx> grad{true, xitab()};
         OpDiv<C, Dx> divo{true, xitab()};
-        OpPrec<C> prec{true, sc, xitab()};
         MidFlux<T, Dx> flux{true, co.Ktab, gid};
-        EpiZ<T> ez{true, dz, dr};
-        ProDir<T> pdir{true, dz, dp, sc};
-        EpiDmgQ<T> eq{true, co, dp, dq};
-        ProUpd<T> pu{true, x, dr, dp, dq, sc};
+        if (!dw) dw = alloc<T>(N);
+        ProPCGCG<T> pdir{true, x, dr, dp, dq, dz, dw, sc};
+        OpPrecGrad<C, Dx> pgrad{true, sc, xitab()};
+        MidFluxU<T, Dx> fluxu{true, co.Ktab, gid, dz};
+        EpiPCGCG<T> ew{true, co.acoef, gid, co.hmul, co.H, dz, dr, dw};
         // FP64: one PCG pass; FP32: passes restarted from the true residual (see mech_solve_t).
         const int passes = kSingle ? 8 : 1;
         const int chunk = 4;
         iters = 0;
         for (int pass = 0; pass < passes; ++pass) {
             init_sc(sc, tol, std::max(1, maxit - iters));
-            // r = rhs - L x
+            // r = rhs - L x (true residual), then the single-reduction iteration
             x_fwd<1>(pi, sc);
             spectral<1, Dx>(grad, sc);
             x_mid<Dx>(flux, sc);
             spectral<Dx, 1>(divo, sc);
             x_inv<1>(EpiDmgRes<T>{true, co, x, dr, rhs, rhs_scale}, sc);
-            // z = M^-1 r
-            x_fwd<1>(ProField<T>{true, dr}, sc);
-            spectral<1, 1>(prec, sc);
-            x_inv<1>(ez, sc);
             auto iter_body = [&] {
                 x_fwd<1>(pdir, sc);
-                spectral<1, Dx>(grad, sc);
-                x_mid<Dx>(flux, sc);
+                spectral<1, Dx + 1>(pgrad, sc);
+                x_mid2<Dx + 1, Dx>(fluxu, sc);
                 spectral<Dx, 1>(divo, sc);
-                x_inv<1>(eq, sc);
-                x_fwd<1>(pu, sc);
-                spectral<1, 1>(prec, sc);
-                x_inv<1>(ez, sc);
+                x_inv<1>(ew, sc);
             };
             if (run_loop(3, x, co.Ktab, sc, iter_body)) {
                 read_sc(sc);

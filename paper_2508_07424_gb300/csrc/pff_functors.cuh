@@ -58,28 +58,6 @@ struct ProStressTotal : MechBase<T, NS> {
     __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
 };
 
-// CG direction update p = r + beta p fused with s = g C : p.
-template <typename T, int NS>
-struct ProCGDir : MechBase<T, NS> {
-    static constexpr int NR = 0;
-    const T *r;
-    T *p;
-    const Scal *scr;
-    __device__ void eval(long long v, T *out, double *) const {
-        const T beta = (T)scr->beta;
-        T u[NS];
-#pragma unroll
-        for (int a = 0; a < NS; ++a) {
-            const size_t i = a * this->N + v;
-            u[a] = r[i] + beta * p[i];
-            p[i] = u[a];
-        }
-        this->stress(v, u, out);
-    }
-    struct Fin { __device__ void operator()(const double *) const {} };
-    __device__ Fin fin(Scal *) const { return Fin{}; }
-};
-
 // ---- spectral tension/compression split (2D plane strain, isotropic lam, mu) ---------------------
 // eps = (a, b, sqrt2 c) in Mandel form, eps_zz = 0. In-plane eigenvalues e1,2 = (a+b)/2 +- r,
 // r = sqrt(((a-b)/2)^2 + c^2), eigenvectors at angle theta with cos 2theta = (a-b)/(2r),
@@ -311,7 +289,7 @@ struct EpiMechInit {
     struct Fin {
         Scal *sc;
         __device__ void operator()(const double *t) const {
-            sc->rr = t[0]; sc->rr0 = t[0]; sc->beta = 0.0; sc->iters = 0;
+            sc->rr = t[0]; sc->rr0 = t[0]; sc->beta = 0.0; sc->alpha = 0.0; sc->first = 1; sc->iters = 0;
             if (!(t[0] <= sc->tol2 * sc->scale2)) sc->done = 0; else sc->done = 1;
             if (!isfinite(t[0])) { sc->flag |= FLAG_NONFINITE; sc->done = 1; }
         }
@@ -375,6 +353,88 @@ struct PwMechUpdate {
             sc->iters += 1;
             if (rrn <= sc->tol2 * sc->scale2 || sc->iters >= sc->max_iters) sc->done = 1;
             if (!isfinite(rrn)) { sc->flag |= FLAG_NONFINITE; sc->done = 1; }
+        }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+// ---- single-reduction CG (Chronopoulos-Gear) for the equilibrium ----------------------------
+// Iteration i holds r_i, w_i = A r_i and the scalars alpha_i, beta_i. The first pass applies
+//   p_i = r_i + beta_i p_{i-1},  s_i = w_i + beta_i s_{i-1},  x += alpha_i p_i,  r_{i+1} = r_i - alpha_i s_i
+// and emits the stress of r_{i+1}; after the projection the last pass stores w_{i+1} = A r_{i+1}
+// and reduces gamma = <r, r> and delta = <w, r> in one go:
+//   beta_{i+1} = gamma_{i+1} / gamma_i,  alpha_{i+1} = gamma_{i+1} / (delta - beta_{i+1} gamma_{i+1} / alpha_i).
+// The first pass after a restart runs with alpha = beta = 0 and only computes w_0.
+template <typename T, int NS>
+struct ProCGCG : MechBase<T, NS> {
+    static constexpr int NR = 0;
+    T *x, *r, *p, *s;
+    const T *w;
+    const Scal *scr;
+    __device__ void eval(long long v, T *out, double *) const {
+        const T al = (T)scr->alpha, be = (T)scr->beta;
+        T rn[NS];
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+            const size_t i = a * this->N + v;
+            const T pi = r[i] + be * p[i];
+            const T si = w[i] + be * s[i];
+            p[i] = pi;
+            s[i] = si;
+            x[i] += al * pi;
+            rn[a] = r[i] - al * si;
+            r[i] = rn[a];
+        }
+        this->stress(v, rn, out);
+    }
+    struct Fin { __device__ void operator()(const double *) const {} };
+    __device__ Fin fin(Scal *) const { return Fin{}; }
+};
+
+template <typename T, int NS>
+struct EpiCGCG {
+    static constexpr int NR = 2;
+    bool skip_if_done;
+    T *w;
+    const T *r;
+    long long N;
+    __device__ void apply(long long v, const T *val, double *acc) const {
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+            const size_t i = a * N + v;
+            w[i] = val[a];
+            const double rv = (double)r[i];
+            acc[0] += rv * rv;
+            acc[1] += (double)val[a] * rv;
+        }
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const {
+            const double gamma = t[0], delta = t[1];
+            sc->rr = gamma;
+            // converged first: an exact solve leaves r = 0 and the next step would be 0 / 0
+            if (isfinite(gamma) && gamma <= sc->tol2 * sc->scale2) {
+                if (!sc->first) sc->iters += 1;
+                sc->first = 0;
+                sc->alpha = 0.0;
+                sc->done = 1;
+                return;
+            }
+            double beta, den;
+            if (sc->first) { beta = 0.0; den = delta; }
+            else { beta = gamma / sc->rz; den = delta - beta * gamma / sc->alpha; }
+            if (!(den > 0.0) || !isfinite(den) || !isfinite(gamma)) {
+                sc->flag |= isfinite(gamma) ? FLAG_BREAKDOWN : FLAG_NONFINITE;
+                sc->done = 1;
+                return;
+            }
+            if (!sc->first) sc->iters += 1;
+            sc->first = 0;
+            sc->alpha = gamma / den;
+            sc->beta = beta;
+            sc->rz = gamma;
+            if (gamma <= sc->tol2 * sc->scale2 || sc->iters >= sc->max_iters) sc->done = 1;
         }
     };
     __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
@@ -478,51 +538,6 @@ struct ProField {
     __device__ Fin fin(Scal *) const { return Fin{}; }
 };
 
-// PCG direction p = z + beta p.
-template <typename T>
-struct ProDir {
-    static constexpr int NR = 0;
-    bool skip_if_done;
-    const T *z;
-    T *p;
-    const Scal *scr;
-    __device__ void eval(long long v, T *out, double *) const {
-        const T pn = z[v] + (T)scr->beta * p[v];
-        p[v] = pn;
-        out[0] = pn;
-    }
-    struct Fin { __device__ void operator()(const double *) const {} };
-    __device__ Fin fin(Scal *) const { return Fin{}; }
-};
-
-// x += alpha p, r -= alpha q, emit r for the preconditioner; reduces <r, r>.
-template <typename T>
-struct ProUpd {
-    static constexpr int NR = 1;
-    bool skip_if_done;
-    T *x, *r;
-    const T *p, *q;
-    const Scal *scr;
-    __device__ void eval(long long v, T *out, double *acc) const {
-        const T al = (T)scr->alpha;
-        x[v] += al * p[v];
-        const T rn = r[v] - al * q[v];
-        r[v] = rn;
-        out[0] = rn;
-        acc[0] += (double)rn * (double)rn;
-    }
-    struct Fin {
-        Scal *sc;
-        __device__ void operator()(const double *t) const {
-            sc->rr = t[0];
-            sc->iters += 1;
-            if (sc->iters >= sc->max_iters && !(t[0] <= sc->tol2 * sc->scale2)) sc->done = 1;
-            if (!isfinite(t[0])) { sc->flag |= FLAG_NONFINITE; sc->done = 1; }
-        }
-    };
-    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
-};
-
 template <typename C, int D>
 struct OpGrad {  // 1 -> D: i xi~_a v^
     typedef typename real_of<C>::type R;
@@ -573,6 +588,132 @@ struct OpPrec {  // v^ / (abar + bbar |xi~|^2)
     }
 };
 
+// ---- single-reduction PCG (Chronopoulos-Gear) for the damage operator -----------------------
+// Iteration i holds r_i, u_i = M^-1 r_i, w_i = L u_i and alpha_i, beta_i. The first pass applies
+//   p_i = u_i + beta_i p_{i-1},  s_i = w_i + beta_i s_{i-1},  x += alpha_i p_i,  r_{i+1} = r_i - alpha_i s_i
+// and transforms r_{i+1}; the spectral pass forms u^ = M^-1 r^ and i xi~ u^ together (the
+// preconditioner costs no transform of its own); the middle x pass stores u and forms the flux
+// K grad u; the last pass stores w = a u - div(flux) and reduces gamma = <r, u>, delta = <w, u>
+// and <r, r> at once:
+//   beta_{i+1} = gamma_{i+1} / gamma_i,  alpha_{i+1} = gamma_{i+1} / (delta - beta_{i+1} gamma_{i+1} / alpha_i).
+template <typename T>
+struct ProPCGCG {
+    static constexpr int NR = 0;
+    bool skip_if_done;
+    T *x, *r, *p, *s;
+    const T *u, *w;
+    const Scal *scr;
+    __device__ void eval(long long v, T *out, double *) const {
+        const T al = (T)scr->alpha, be = (T)scr->beta;
+        const T pi = u[v] + be * p[v];
+        const T si = w[v] + be * s[v];
+        p[v] = pi;
+        s[v] = si;
+        x[v] += al * pi;
+        const T rn = r[v] - al * si;
+        r[v] = rn;
+        out[0] = rn;
+    }
+    struct Fin { __device__ void operator()(const double *) const {} };
+    __device__ Fin fin(Scal *) const { return Fin{}; }
+};
+
+template <typename C, int D>
+struct OpPrecGrad {  // r^ -> [u^ = r^ / (abar + bbar |xi~|^2), i xi~_a u^]
+    typedef typename real_of<C>::type R;
+    bool skip_if_done;
+    const Scal *scr;
+    XiTab<R> xi;
+    __device__ void apply(const Geom &g, int kx, int ky, int kz, const C *in, C *out) const {
+        R xs[3];
+        xi.get(kx, ky, kz, xs[0], xs[1], xs[2]);
+        const R q2 = xs[0] * xs[0] + xs[1] * xs[1] + xs[2] * xs[2];
+        const R sc = (R)1 / ((R)scr->abar + (R)scr->bbar * q2);
+        const R ux = in[0].x * sc, uy = in[0].y * sc;
+        out[0].x = ux;
+        out[0].y = uy;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            out[1 + a].x = -xs[a] * uy;
+            out[1 + a].y = xs[a] * ux;
+        }
+    }
+};
+
+template <typename T, int D>
+struct MidFluxU {  // [u, grad u] -> store u, K grad u
+    bool skip_if_done;
+    const T *Ktab;
+    const int *gid;
+    T *u;
+    __device__ void apply(long long v, const T *in, T *out) const {
+        u[v] = in[0];
+        const T *K = Ktab + (size_t)gid[v] * 6;
+        if constexpr (D == 2) {
+            out[0] = K[0] * in[1] + K[2] * in[2];
+            out[1] = K[2] * in[1] + K[1] * in[2];
+        } else {
+            out[0] = K[0] * in[1] + K[5] * in[2] + K[4] * in[3];
+            out[1] = K[5] * in[1] + K[1] * in[2] + K[3] * in[3];
+            out[2] = K[4] * in[1] + K[3] * in[2] + K[2] * in[3];
+        }
+    }
+};
+
+template <typename T> struct DmgCoef;
+
+template <typename T>
+struct EpiPCGCG {
+    static constexpr int NR = 3;
+    bool skip_if_done;
+    const T *acoef;
+    const int *gid;
+    T hmul;
+    const T *H;
+    const T *u, *r;
+    T *w;
+    __device__ void apply(long long v, const T *val, double *acc) const {
+        const T a = acoef[gid[v]] + (hmul != (T)0 ? hmul * H[v] : (T)0);
+        const T uv = u[v];
+        const T wv = a * uv - val[0];
+        w[v] = wv;
+        const double rv = (double)r[v];
+        acc[0] += rv * (double)uv;
+        acc[1] += (double)wv * (double)uv;
+        acc[2] += rv * rv;
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const {
+            const double gamma = t[0], delta = t[1];
+            sc->rr = t[2];
+            // converged first: an exact solve leaves r = 0 and the next step would be 0 / 0
+            if (isfinite(t[2]) && t[2] <= sc->tol2 * sc->scale2) {
+                if (!sc->first) sc->iters += 1;
+                sc->first = 0;
+                sc->alpha = 0.0;
+                sc->done = 1;
+                return;
+            }
+            double beta, den;
+            if (sc->first) { beta = 0.0; den = delta; }
+            else { beta = gamma / sc->rz; den = delta - beta * gamma / sc->alpha; }
+            if (!(den > 0.0) || !isfinite(den) || !isfinite(t[2])) {
+                sc->flag |= isfinite(t[2]) ? FLAG_BREAKDOWN : FLAG_NONFINITE;
+                sc->done = 1;
+                return;
+            }
+            if (!sc->first) sc->iters += 1;
+            sc->first = 0;
+            sc->alpha = gamma / den;
+            sc->beta = beta;
+            sc->rz = gamma;
+            if (t[2] <= sc->tol2 * sc->scale2 || sc->iters >= sc->max_iters) sc->done = 1;
+        }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
 template <typename T, int D>
 struct MidFlux {  // grad v -> K grad v
     bool skip_if_done;
@@ -610,56 +751,9 @@ struct EpiDmgRes {
     struct Fin {
         Scal *sc;
         __device__ void operator()(const double *t) const {
-            sc->rr = t[0]; sc->rr0 = t[0]; sc->iters = 0; sc->first = 1; sc->beta = 0.0;
+            sc->rr = t[0]; sc->rr0 = t[0]; sc->iters = 0; sc->first = 1; sc->beta = 0.0; sc->alpha = 0.0;
             if (t[0] <= sc->tol2 * sc->scale2) sc->done = 1;
             if (!isfinite(t[0])) { sc->flag |= FLAG_NONFINITE; sc->done = 1; }
-        }
-    };
-    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
-};
-
-// z = M^-1 r; reduces <r, z>; beta and the convergence test.
-template <typename T>
-struct EpiZ {
-    static constexpr int NR = 1;
-    bool skip_if_done;
-    T *z;
-    const T *r;
-    __device__ void apply(long long v, const T *val, double *acc) const {
-        z[v] = val[0];
-        acc[0] += (double)r[v] * (double)val[0];
-    }
-    struct Fin {
-        Scal *sc;
-        __device__ void operator()(const double *t) const {
-            if (sc->first) { sc->beta = 0.0; sc->first = 0; }
-            else sc->beta = t[0] / sc->rz;
-            sc->rz = t[0];
-            if (sc->rr <= sc->tol2 * sc->scale2) sc->done = 1;
-        }
-    };
-    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
-};
-
-// q = a p - div; reduces <p, q>; alpha = rz / pq.
-template <typename T>
-struct EpiDmgQ {
-    static constexpr int NR = 1;
-    bool skip_if_done;
-    DmgCoef<T> co;
-    const T *p;
-    T *q;
-    __device__ void apply(long long v, const T *val, double *acc) const {
-        const T qv = co.a(v) * p[v] - val[0];
-        q[v] = qv;
-        acc[0] += (double)p[v] * (double)qv;
-    }
-    struct Fin {
-        Scal *sc;
-        __device__ void operator()(const double *t) const {
-            sc->pq = t[0];
-            if (!(t[0] > 0.0) || !isfinite(t[0])) { sc->flag |= FLAG_BREAKDOWN; sc->done = 1; }
-            else sc->alpha = sc->rz / t[0];
         }
     };
     __device__ Fin fin(Scal *sc) const { return Fin{sc}; }

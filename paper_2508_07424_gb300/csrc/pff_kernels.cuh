@@ -135,10 +135,13 @@ __global__ void __launch_bounds__(512) k_x_inv(Geom g, const typename cplx_of<T>
 }
 
 // ---- x-axis inverse, pointwise map, x-axis forward ----------------------------------------------
-template <typename T, int NC, class Mid>
+// Inverse x pass of NCI components, mid.apply(v, in[NCI], out[NCO]) per voxel (NCO <= NCI), forward
+// x pass of the NCO outputs.
+template <typename T, int NCI, int NCO, class Mid>
 __global__ void __launch_bounds__(512) k_x_mid(Geom g, typename cplx_of<T>::type *__restrict__ spec, Mid mid,
                                                const typename cplx_of<T>::type *__restrict__ tw, Scal *sc) {
     typedef typename cplx_of<T>::type C;
+    static_assert(NCO <= NCI, "k_x_mid maps NCI components to at most NCI");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *s = reinterpret_cast<C *>(smem_raw);
     if (mid.skip_if_done && sc->done) return;
@@ -149,18 +152,18 @@ __global__ void __launch_bounds__(512) k_x_mid(Geom g, typename cplx_of<T>::type
     const int ppp = g.ny >> 1;
     const int z = (int)(pair / ppp), y0 = 2 * (int)(pair % ppp);
     const long long row0 = ((long long)z * g.ny + y0) * nx;
-    C *line = s + (size_t)rp * NC * nx;
+    C *line = s + (size_t)rp * NCI * nx;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) load_packed<T, C>(g, spec, c, z, y0, line + c * nx, t, TL);
+    for (int c = 0; c < NCI; ++c) load_packed<T, C>(g, spec, c, z, y0, line + c * nx, t, TL);
     __syncthreads();
-    fft_lines<C, NC>(s, nx, g.lx, NC, NC, 1, tw, true);
+    fft_lines<C, NCI>(s, nx, g.lx, NCI, NCI, 1, tw, true);
     const T sN = (T)g.invN;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int x = t + q * TL;
-        T va[NC], vb[NC], oa[NC], ob[NC];
+        T va[NCI], vb[NCI], oa[NCO], ob[NCO];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
+        for (int c = 0; c < NCI; ++c) {
             const C v = line[c * nx + x];
             va[c] = v.x * sN;
             vb[c] = v.y * sN;
@@ -168,15 +171,15 @@ __global__ void __launch_bounds__(512) k_x_mid(Geom g, typename cplx_of<T>::type
         mid.apply(row0 + x, va, oa);
         mid.apply(row0 + nx + x, vb, ob);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) line[c * nx + x] = cmk<C>(oa[c], ob[c]);
+        for (int c = 0; c < NCO; ++c) line[c * nx + x] = cmk<C>(oa[c], ob[c]);
     }
     __syncthreads();
-    fft_lines<C, NC>(s, nx, g.lx, NC, NC, 1, tw, false);
+    fft_lines<C, NCI>(s, nx, g.lx, NCO, NCI, 1, tw, false);
     const int nh = (nx >> 1) + 1;
     for (int k = t; k < nh; k += TL) {
         const int km = (nx - k) & (nx - 1);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
+        for (int c = 0; c < NCO; ++c) {
             const C Z = line[c * nx + k], Zm = line[c * nx + km];
             C Xa, Xb;
             Xa.x = (T)0.5 * (Z.x + Zm.x);
