@@ -109,6 +109,9 @@ WORKLOADS = {
                             "16 voxels at mid-height, dtau=1.5*Gc*A_g/100",
     "polycrystal_1024": "1024x1024 periodic Voronoi polycrystal, 200 grains, cubic C11=1 C12=0.6 C44=0.5 (Zener 2.5), "
                         "uniform in-plane orientations, cleavage beta=2, l=2, CTE crack 102 voxels, dtau=1.5*A_g/400",
+    "polycrystal_plate_256": "256x128x1 polycrystal plate (six strain components), 60 Laguerre grains with lognormal "
+                             "size spread 0.25, SO(3)-uniform orientations, cubic C1111:C1122=24:8 with Zener 4, "
+                             "cleavage beta=2, l=2, CTE crack 26 voxels, dtau=1.5*A_g/200",
     "batched_3d_polycrystals": "16 periodic Voronoi 3D polycrystals, grids drawn from {32,64,128}^3, 50-200 grains, "
                                "cubic C11=1 C12=0.6 C44=0.5 with SO(3)-uniform orientations, lognormal Gc (sigma 0.3), "
                                "l=2, through CTE crack 0.1 n, dtau=1.5*<Gc>*A_g/100; run as 16 concurrent streams",
@@ -121,6 +124,8 @@ def make_workload(rank, precision, name=WORKLOAD):
         w = synth.homogeneous_plate_64()
     elif name == "polycrystal_1024":
         w = synth.polycrystal_1024(seed=2 + rank)
+    elif name == "polycrystal_plate_256":
+        w = synth.polycrystal_plate_256(seed=5 + rank)
     else:
         w = synth.fibre_composite_512(seed=1 + rank)
     w.precision = precision

@@ -64,7 +64,8 @@ enum {
 /* Solver configuration (rve_config_default fills every field). */
 typedef struct {
     int dim;               /* 2 (plane strain) or 3 */
-    int n[3];              /* grid; n[2] = 1 when dim = 2 */
+    int n[3];              /* grid; n[2] = 1 when dim = 2; dim = 3 takes n[2] = 1 for the one-voxel-thick
+                              plates of Sec. 5 (six strain components, xi_z = 0) */
     double ell;            /* phase-field length l in voxels (Eq. (CrackLenght)) */
     double k_res;          /* residual stiffness k of g(phi) = (1 - phi)^2 + k (Sec. 2.1) */
     int split;             /* RVE_SPLIT_NONE (the paper's psi_o) or RVE_SPLIT_SPECTRAL */
@@ -112,12 +113,15 @@ typedef struct {
     int fractured;      /* 1 once Sigma^n <= fracture_ratio * max Sigma */
     double stag_err;    /* final staggered error of Eq. (errors_crack) */
     int flags;          /* RVE_STEP_STAGNATED: accepted at the staggered noise floor (no improvement
-                           for 20 iterations, error within 100 x tol_stag); RVE_STEP_CUTBACK: the
+                           for 20 iterations, error within 1000 x tol_stag); RVE_STEP_CUTBACK: the
                            staggered iteration failed and the increment was split into halves
                            (up to 4 levels), each committed as its own load-curve point; the
                            iteration counts then cover every attempt; RVE_STEP_UNCONVERGED: even
                            the deepest split did not converge and its last staggered iterate was
                            kept (the increment is still a point of D = tau^n) */
+    double G_inst;      /* instantaneous energy release rate of Eq. (Gmed),
+                           V (T^n - T^{n-1}) / (Gamma^n - Gamma^{n-1}), with T^0 = 0 and Gamma^0
+                           the crack surface of the initial crack; NaN when Gamma did not change */
 } rve_step_result;
 
 enum { RVE_STEP_STAGNATED = 1, RVE_STEP_CUTBACK = 2, RVE_STEP_UNCONVERGED = 4 };
@@ -127,6 +131,8 @@ typedef struct {
     int n;
     double E, tau, T, Sigma, Sigma_max, tau0;
     int fractured;
+    double D, Gamma;    /* D(phi^n) and Gamma(phi^n) of the committed state (D = tau0, Gamma of the
+                           initial crack before the first increment) */
 } rve_scalars;
 
 void rve_config_default(rve_config *cfg);
@@ -154,6 +160,13 @@ int step_dissipation(rve_handle h, double dtau, rve_step_result *out);
 /* Effective toughness of Eqs. (JaviGc)/(ABC): G = V / A_g (T^F - 1/2 Sigma^F E^F), V = voxel
  * count, A_g = (nx - crack_len) (x nz in 3D). RVE_ENOTFRACTURED until the fracture point. */
 int effective_toughness(rve_handle h, double *g_eff);
+
+/* Toughness from the dissipation functional (Eq. (CrackLenght_ani)) instead of the load curve, the
+ * measure Sec. 5.1 compares against it: (D(phi^F) - D(phi^0)) / A_g. Without history (variational
+ * model) the two measures agree up to the trapezoid error and the change of the enrichment energy;
+ * with history the load-curve measure is the one that counts the dissipated energy.
+ * RVE_ENOTFRACTURED until the fracture point. */
+int effective_toughness_functional(rve_handle h, double *g_eff);
 
 /* Copy a device field to / from a host buffer of n doubles (see RVE_FIELD_*). Setting PHI, H or
  * FLUCT1 lets a caller inject a committed state; setting PHI also copies it to the trial field. */

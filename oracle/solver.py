@@ -279,6 +279,8 @@ class State:
     Sigma_max: float = 0.0
     n: int = 0
     fractured: bool = False
+    tau0: float = 0.0              # D(phi^0), the functional of the initial crack
+    Gamma0: float = 0.0            # Gamma(phi^0), its crack surface
     curve: list = field(default_factory=list)
 
     def copy(self):
@@ -293,6 +295,7 @@ def init_state(model):
     st = State(phi=phi_ini, H=psi_ini.copy(), psi_ini=psi_ini, F1=z.copy(), eps=z.copy())
     st.tau = model.dissipation(phi_ini)
     st.tau0 = st.tau
+    st.Gamma0 = model.crack_surface(phi_ini)
     return st
 
 
@@ -463,13 +466,35 @@ def increment(model, st, dtau, anderson_m=5, accept_unconverged=False):
     return new, stats
 
 
-def toughness(model, st):
-    """Eq. (JaviGc) with Eq. (ABC): G = V / A_g (T^F - 1/2 Sigma^F E^F)."""
+def crack_area(model):
+    """A_g of Eq. (JaviGc0): the surface the fracture creates, without the pre-crack (h = 1)."""
     micro = model.micro
     nx, ny, nz = micro.n
     a0 = micro.crack.length if micro.crack.kind != 0 else 0
-    A_g = (nx - a0) * (nz if micro.dim == 3 else 1)
-    return model.V / A_g * (st.T - 0.5 * st.Sigma * st.E)
+    return (nx - a0) * (nz if micro.dim == 3 else 1)
+
+
+def toughness(model, st):
+    """Eq. (JaviGc) with Eq. (ABC): G = V / A_g (T^F - 1/2 Sigma^F E^F)."""
+    return model.V / crack_area(model) * (st.T - 0.5 * st.Sigma * st.E)
+
+
+def toughness_functional(model, st):
+    """Toughness from the dissipation functional instead of the load curve (Sec. 5.1, the
+    comparison with the variational model): (D(phi^F) - D(phi^0)) / A_g, D of Eq.
+    (CrackLenght_ani) and D(phi^0) = tau^0 the functional of the initial crack."""
+    return (model.dissipation(st.phi) - st.tau0) / crack_area(model)
+
+
+def instantaneous_toughness(model, Gamma0, curve):
+    """Eq. (Gmed): G^n = V (T^n - T^{n-1}) / (Gamma^n - Gamma^{n-1}) for each committed increment,
+    with T^0 = 0 and Gamma^0 the crack surface (Eq. (CrackLenghtreal)) of the initial crack."""
+    out, T0, G0 = [], 0.0, Gamma0
+    for rec in curve:
+        dG = rec["Gamma"] - G0
+        out.append(model.V * (rec["T"] - T0) / dG if dG != 0.0 else float("nan"))
+        T0, G0 = rec["T"], rec["Gamma"]
+    return out
 
 
 def params_from_workload(w, **kw):

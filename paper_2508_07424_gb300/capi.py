@@ -35,12 +35,14 @@ class rve_step_result(C.Structure):
     _fields_ = [("n", C.c_int), ("E", C.c_double), ("Sigma", C.c_double), ("D", C.c_double),
                 ("Emec", C.c_double), ("T", C.c_double), ("Gamma", C.c_double), ("tau", C.c_double),
                 ("mech_iters", C.c_int), ("dmg_iters", C.c_int), ("root_evals", C.c_int),
-                ("stag_iters", C.c_int), ("fractured", C.c_int), ("stag_err", C.c_double), ("flags", C.c_int)]
+                ("stag_iters", C.c_int), ("fractured", C.c_int), ("stag_err", C.c_double), ("flags", C.c_int),
+                ("G_inst", C.c_double)]
 
 
 class rve_scalars(C.Structure):
     _fields_ = [("n", C.c_int), ("E", C.c_double), ("tau", C.c_double), ("T", C.c_double),
-                ("Sigma", C.c_double), ("Sigma_max", C.c_double), ("tau0", C.c_double), ("fractured", C.c_int)]
+                ("Sigma", C.c_double), ("Sigma_max", C.c_double), ("tau0", C.c_double), ("fractured", C.c_int),
+                ("D", C.c_double), ("Gamma", C.c_double)]
 
 
 class rve_request_result(C.Structure):
@@ -60,6 +62,7 @@ _SIGS = {
     "set_microstructure": (C.c_int, [rve_handle, C.POINTER(rve_micro)]),
     "step_dissipation": (C.c_int, [rve_handle, C.c_double, C.POINTER(rve_step_result)]),
     "effective_toughness": (C.c_int, [rve_handle, _dp]),
+    "effective_toughness_functional": (C.c_int, [rve_handle, _dp]),
     "rve_get_field": (C.c_int, [rve_handle, C.c_int, _dp, C.c_size_t]),
     "rve_set_field": (C.c_int, [rve_handle, C.c_int, _dp, C.c_size_t]),
     "rve_get_scalars": (C.c_int, [rve_handle, C.POINTER(rve_scalars)]),

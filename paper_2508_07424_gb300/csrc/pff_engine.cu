@@ -330,10 +330,16 @@ struct PwAAGram {
     AAPtrs h;
     int K;  // number of differences (history length - 1)
     __device__ void apply(long long v, double *acc) const {
-        double R[6];
-        for (int j = 0; j <= K; ++j) R[j] = h.G[j][v] - h.X[j][v];
+        // fixed trip counts with guards keep R and dF in registers
+        double R[6], RK = 0.0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            R[j] = j <= K ? h.G[j][v] - h.X[j][v] : 0.0;
+            if (j == K) RK = R[j];
+        }
         double dF[5];
-        for (int a = 0; a < K; ++a) dF[a] = R[a + 1] - R[a];
+#pragma unroll
+        for (int a = 0; a < 5; ++a) dF[a] = a < K ? R[a + 1] - R[a] : 0.0;
         int idx = 0;
 #pragma unroll
         for (int a = 0; a < 5; ++a)
@@ -344,7 +350,7 @@ struct PwAAGram {
             }
 #pragma unroll
         for (int a = 0; a < 5; ++a)
-            if (a < K) acc[15 + a] += dF[a] * R[K];
+            if (a < K) acc[15 + a] += dF[a] * RK;
     }
     struct Fin {
         Scal *sc;
@@ -601,10 +607,9 @@ struct EngineBase {
     virtual void load_state(const char *p) = 0;
     virtual void timing_reset() = 0;
     virtual void timing_get(double &ms, long &n, double &bytes) = 0;
-    double toughness_value() const {
-        const double Ag = (double)(g.nx - crack_len_) * (D == 3 ? g.nz : 1);
-        return (double)N / Ag * (S.T - 0.5 * S.Sigma * S.E);
-    }
+    double crack_area() const { return (double)(g.nx - crack_len_) * (D == 3 ? g.nz : 1); }
+    double toughness_value() const { return (double)N / crack_area() * (S.T - 0.5 * S.Sigma * S.E); }
+    double toughness_functional_value() const { return (S.D - S.tau0) / crack_area(); }
 };
 
 template <typename T>
@@ -947,9 +952,11 @@ struct Engine : EngineBase {
         CK(cudaGetLastError());
         ++launches;
     }
-    // Spectral passes between the x passes: 2D one y pass; 3D y, z (with the operator), y.
+    // Spectral passes between the x passes: 2D one y pass; 3D y, z (with the operator), y. A 3D
+    // grid one voxel thick (nz = 1, the plates of Sec. 5) has xi_z = 0 everywhere and needs no z
+    // transform: the operator runs in the y pass, as in 2D, with all NS components.
     template <int NCI, int NCO, class Op> void spectral(const Op &op, Scal *s, bool timed = false) {
-        if (D == 2) {
+        if (D == 2 || g.nz == 1) {
             axis<NCI, NCO, AX_FWD_OP_INV>(1, op, s, timed);
         } else {
             OpNone<C> nop{op.skip_if_done};
@@ -1235,13 +1242,13 @@ struct Engine : EngineBase {
         CK(cudaMemsetAsync(mx, 0, sizeof(T) * NS * N, st));
         CK(cudaMemsetAsync(eps_com, 0, sizeof(double) * NS * N, st));
         CK(cudaMemsetAsync(psi1, 0, sizeof(T) * N, st));
-        double tau0 = 0.0;
+        double tau0 = 0.0, Gamma0 = 0.0;
         if (m->crack_kind == RVE_CRACK_NONE) {
             CK(cudaMemsetAsync(phi, 0, sizeof(T) * N, st));
             CK(cudaMemsetAsync(psi_ini, 0, sizeof(T) * N, st));
             CK(cudaMemsetAsync(H, 0, sizeof(T) * N, st));
         } else {
-            int rc = cte_init(m->crack_phi_M, tau0);
+            int rc = cte_init(m->crack_phi_M, tau0, Gamma0);
             if (rc) return rc;
         }
         CK(cudaMemcpyAsync(phi_trial, phi, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
@@ -1250,6 +1257,8 @@ struct Engine : EngineBase {
         S = rve_scalars{};
         S.tau = tau0;
         S.tau0 = tau0;
+        S.D = tau0;
+        S.Gamma = Gamma0;
         curve.clear();
         micro_set = true;
         return RVE_OK;
@@ -1257,7 +1266,7 @@ struct Engine : EngineBase {
 
     // phi_o - l^2 div(A grad phi_o) = phi_disc (Eqs. (damini), (daminiAni), read with l^2),
     // phi_ini = phi_M phi_o / max phi_o, psi_ini = max(0, gamma'(phi_ini) / (2 (1 - phi_ini))) (Eq. (Enini)).
-    int cte_init(double phi_M, double &tau0) {
+    int cte_init(double phi_M, double &tau0, double &Gamma0) {
         T *phi_disc_T = tmpf;
         k_cast_copy<T><<<(int)((N + 255) / 256), 256, 0, st>>>(N, phi_disc, phi_disc_T);
         ++launches;
@@ -1284,8 +1293,7 @@ struct Engine : EngineBase {
         DmgCoef<T> co0{acoef, Ktab, gid, (T)0.0, Hcur};
         if (D == 2) apply_L<2>(co0, phi, tmpf); else apply_L<3>(co0, phi, tmpf);
         pointwise(PwPsiIni<T>{false, tmpf, phi, psi_ini, H}, sc2);
-        double Gm;
-        dissipation(phi, tau0, Gm);
+        dissipation(phi, tau0, Gamma0);
         return RVE_OK;
     }
     template <int Dx> void apply_L(const DmgCoef<T> &co, const T *v, T *out) {
@@ -1522,7 +1530,11 @@ struct Engine : EngineBase {
         const double Emec = h_sc->red[5];
         double Dc, Gc_;
         dissipation(phi, Dc, Gc_);
-        S.T += 0.5 * (Sigma + S.Sigma) * (E - S.E);
+        const double dT = 0.5 * (Sigma + S.Sigma) * (E - S.E), dG = Gc_ - S.Gamma;
+        r.G_inst = dG != 0.0 ? (double)N * dT / dG : NAN;  // Eq. (Gmed)
+        S.T += dT;
+        S.D = Dc;
+        S.Gamma = Gc_;
         S.Sigma = Sigma;
         S.Sigma_max = std::max(S.Sigma_max, Sigma);
         S.E = E;
@@ -1715,7 +1727,7 @@ int rve_create(const rve_config *cfg, rve_handle *out) {
     if (cfg->dim != 2 && cfg->dim != 3) return RVE_EINVAL;
     if (!pow2_in(cfg->n[0], 4, 1024) || !pow2_in(cfg->n[1], 4, 1024)) return RVE_EINVAL;
     if (cfg->dim == 2 && cfg->n[2] != 1) return RVE_EINVAL;
-    if (cfg->dim == 3 && !pow2_in(cfg->n[2], 4, 1024)) return RVE_EINVAL;
+    if (cfg->dim == 3 && cfg->n[2] != 1 && !pow2_in(cfg->n[2], 4, 1024)) return RVE_EINVAL;
     if ((long long)cfg->n[0] * cfg->n[1] * cfg->n[2] > (1LL << 24)) return RVE_EINVAL;
     if (!(cfg->ell > 0) || cfg->k_res < 0 || cfg->anderson_m < 0 || cfg->anderson_m > 5) return RVE_EINVAL;
     if (cfg->split != RVE_SPLIT_NONE && cfg->split != RVE_SPLIT_SPECTRAL) return RVE_EINVAL;
@@ -1756,6 +1768,14 @@ int effective_toughness(rve_handle h, double *g_eff) {
     if (!h->e->micro_set) return RVE_ESTATE;
     if (!h->e->S.fractured) return RVE_ENOTFRACTURED;
     *g_eff = h->e->toughness_value();
+    return RVE_OK;
+}
+
+int effective_toughness_functional(rve_handle h, double *g_eff) {
+    if (!h || !g_eff) return RVE_EINVAL;
+    if (!h->e->micro_set) return RVE_ESTATE;
+    if (!h->e->S.fractured) return RVE_ENOTFRACTURED;
+    *g_eff = h->e->toughness_functional_value();
     return RVE_OK;
 }
 

@@ -86,6 +86,11 @@ class Rve:
         capi.check(capi.lib().effective_toughness(self.h, C.byref(g)), "effective_toughness")
         return g.value
 
+    def toughness_functional(self):
+        g = C.c_double()
+        capi.check(capi.lib().effective_toughness_functional(self.h, C.byref(g)), "effective_toughness_functional")
+        return g.value
+
     def get(self, field):
         n = self.nvox * (self.ns if field in _FIELD_TENSOR else 1)
         a = np.empty(n, np.float64)

@@ -273,6 +273,55 @@ def voronoi(n, n_grains, seed, C=(1.0, 0.6, 0.5), orientation="inplane", Gc0=1.0
                   beta=[beta] * n_grains, crack=crack, name=name)
 
 
+def laguerre_ids(n, n_grains, seed, sigma_size=0.25):
+    """Grain ids (ny, nx) of a periodic Laguerre (power-weighted Voronoi) tessellation.
+
+    Seeds are uniform in the cell; seed i gets the radius r_i = r_mean exp(s z_i - s^2 / 2),
+    z_i ~ N(0, 1), s = sigma_size, r_mean half the mean seed spacing, and a voxel centre x joins
+    the grain minimising |x - x_i|^2 - r_i^2 (minimum-image distance). Lognormal radii give a
+    lognormal grain-size spread; sigma_size = 0 is the plain Voronoi tessellation. Ties go to the
+    lowest seed index. Returns (gid, seeds, radii).
+    """
+    nx, ny = n
+    rng = np.random.default_rng(seed)
+    seeds = rng.uniform(0.0, 1.0, (n_grains, 2)) * np.array([nx, ny], np.float64)
+    r_mean = 0.5 * np.sqrt(nx * ny / n_grains)
+    radii = r_mean * np.exp(sigma_size * rng.standard_normal(n_grains) - 0.5 * sigma_size ** 2)
+    x = np.arange(nx) + 0.5
+    y = np.arange(ny) + 0.5
+    best = np.full((ny, nx), np.inf)
+    gid = np.zeros((ny, nx), np.int32)
+    for i in range(n_grains):
+        dx = np.abs(x - seeds[i, 0])
+        dx = np.minimum(dx, nx - dx)
+        dy = np.abs(y - seeds[i, 1])
+        dy = np.minimum(dy, ny - dy)
+        pd = dy[:, None] ** 2 + dx[None, :] ** 2 - radii[i] ** 2
+        upd = pd < best
+        best[upd] = pd[upd]
+        gid[upd] = i
+    return gid, seeds, radii, rng
+
+
+def polycrystal_plate(n=(256, 128), n_grains=60, seed=5, zener=4.0, beta=2.0, sigma_size=0.25,
+                      orientation="so3", Gc0=1.0, crack=None, name="polycrystal_plate"):
+    """Polycrystal plate one voxel thick, (nx, ny, 1) with six strain components (Sec. 5).
+
+    Laguerre grains (``laguerre_ids``) with orientations uniform on SO(3) (three Euler angles'
+    worth) or about z ('inplane'); cubic stiffness with C1111 : C1122 = 24 : 8 and C1212 from the
+    Zener ratio z = 2 C1212 / (C1111 - C1122) (Eq. (zener)), scaled to C1111 = 1; one cleavage
+    plane with normal R e1 and contrast beta (Eq. (PFFani)). With nz = 1 the damage gradient has
+    no z component, so A acts through the in-plane projection of the normal.
+    """
+    nx, ny = n
+    gid, _, _, rng = laguerre_ids(n, n_grains, seed, sigma_size)
+    c11, c12 = 1.0, 8.0 / 24.0
+    C = (c11, c12, 0.5 * zener * (c11 - c12))
+    R = so3_rotations(n_grains, rng) if orientation == "so3" else inplane_rotations(n_grains, rng)
+    return _micro((nx, ny, 1), 3, gid.reshape(1, ny, nx), [C] * n_grains, R=R, Gc=np.full(n_grains, Gc0),
+                  cleave=[(1.0, 0.0, 0.0)] * n_grains, beta=[beta] * n_grains, crack=crack, name=name)
+
+
 def _dtau(kappa, gc_ref, a_g, n_inc):
     return kappa * gc_ref * a_g / n_inc
 
@@ -325,6 +374,18 @@ def polycrystal_3d(n, n_grains, seed, n_inc=100, sigma_Gc=0.3, precision="fp32r"
     w = Workload(m, ell=2.0, k_res=1e-6, split=0, n_inc=n_inc, precision=precision,
                  name=f"polycrystal3d_{n}")
     w.dtau = _dtau(1.5, float(np.mean(m.Gc)), w.A_g, n_inc)
+    return w
+
+
+def polycrystal_plate_256(n_inc=200, seed=5, zener=4.0, beta=2.0, precision="fp64"):
+    """The polycrystal plate of Sec. 5 at power-of-two size: 256 x 128 x 1 voxels, 60 Laguerre
+    grains with lognormal size spread 0.25, SO(3) orientations, Zener ratio 4, cleavage beta = 2,
+    ell = 2, CTE crack of 0.1 Lx at mid-height."""
+    a0 = 26
+    crack = Crack(CRACK_CTE, row=64, x0=0, length=a0, phi_M=0.8, stiffness=1e-6)
+    m = polycrystal_plate((256, 128), 60, seed, zener, beta, crack=crack, name="polycrystal_plate_256")
+    w = Workload(m, ell=2.0, k_res=1e-6, split=0, n_inc=n_inc, precision=precision, name="polycrystal_plate_256")
+    w.dtau = _dtau(1.5, 1.0, w.A_g, n_inc)
     return w
 
 
@@ -411,6 +472,11 @@ def small_cases():
     w = Workload(m, ell=2.0, split=0, n_inc=6, name="poly3d16x16x8")
     w.dtau = _dtau(1.5, float(np.mean(m.Gc)), w.A_g, 24)
     cases["poly3d"] = w
+    crack = Crack(CRACK_CTE, row=8, x0=0, length=4, phi_M=0.8, stiffness=1e-6)
+    m = polycrystal_plate((32, 16), 8, 17, zener=4.0, beta=2.0, crack=crack, name="plate32x16")
+    w = Workload(m, ell=2.0, split=0, n_inc=6, name="plate32x16x1")
+    w.dtau = _dtau(1.5, 1.0, w.A_g, 24)
+    cases["plate3d"] = w
     return cases
 
 

@@ -221,6 +221,69 @@ def test_uniform_branch_closed_form():
         assert abs(st.T - T) < 1e-11 * T
 
 
+def test_instantaneous_toughness_uniform_branch():
+    """Eq. (Gmed) on the uniform branch, where every quantity is closed form: with phi uniform the
+    crack surface is Gamma = V phi^2 / (2 l) (no gradient term), T follows the closed-form load
+    curve of the test above, and G^n = V (T^n - T^{n-1}) / (Gamma^n - Gamma^{n-1})."""
+    model = _uniform_case()
+    st = S.init_state(model)
+    assert st.Gamma0 == 0.0
+    V, Gc, ell, k = model.V, 1.0, 2.0, 1e-6
+    M = synth.iso_constants(1.0, 0.3)[0]
+    dtau = 0.05 * V
+    T, Sig0, E0, Gam0, ref = 0.0, 0.0, 0.0, 0.0, []
+    for n in range(1, 5):
+        st, _ = S.increment(model, st, dtau)
+        phi = math.sqrt(2 * ell * n * dtau / (Gc * V))
+        E = math.sqrt(Gc * phi / (ell * (1 - phi) * M))
+        Sig = ((1 - phi) ** 2 + k) * M * E
+        Tn = T + 0.5 * (Sig + Sig0) * (E - E0)
+        Gam = V * phi * phi / (2 * ell)
+        ref.append(V * (Tn - T) / (Gam - Gam0))
+        T, Sig0, E0, Gam0 = Tn, Sig, E, Gam
+    got = S.instantaneous_toughness(model, st.Gamma0, st.curve)
+    assert np.allclose(got, ref, rtol=1e-10, atol=0), (got, ref)
+
+
+def test_residual_energy_is_half_sigma_e():
+    """E_res of Eq. (JaviGc) is read as 1/2 Sigma^F E^F (Eq. (ABC)): at an equilibrium state the
+    stored energy is 1/2 V <sigma : eps> = 1/2 V E <sigma> : f, because the periodic fluctuation
+    does no work against a divergence-free stress (Hill-Mandel). With it the load-curve toughness
+    equals (V T - E_mec) / A_g."""
+    w = synth.small_cases()["fibre64x16"]
+    model = S.Model(w.micro, S.params_from_workload(w, tol_stag=1e-11))
+    st = S.init_state(model)
+    for _ in range(3):
+        st, _ = S.increment(model, st, w.dtau)
+        rec = st.curve[-1]
+        assert abs(rec["Emec"] - 0.5 * model.V * st.Sigma * st.E) < 1e-8 * rec["Emec"]
+    g_work = S.toughness(model, st)
+    assert abs(g_work - (model.V * st.T - st.curve[-1]["Emec"]) / S.crack_area(model)) < 1e-8 * abs(g_work)
+
+
+def test_work_and_functional_toughness_agree_without_history():
+    """Sec. 5.1: for the model without history (variational up to the enrichment term) the
+    load-curve measure and the functional measure of the toughness coincide; their gap is the
+    trapezoid error of the curve plus the change of the enrichment energy int g(phi) psi_ini, and
+    the first part shrinks when the increment does."""
+    crack = synth.Crack(synth.CRACK_CTE, row=8, x0=0, length=4, phi_M=0.8)
+    m = synth.homogeneous((16, 16), crack=crack)
+    gaps = []
+    for steps, dtau in ((6, 0.2), (12, 0.1), (24, 0.05)):
+        model = S.Model(m, S.Params(ell=2.0, history=False, tol_stag=1e-11))
+        st = S.init_state(model)
+        k = model.p.k_res
+        ini0 = float(np.sum(mat.degradation(st.phi, k) * st.psi_ini))
+        for _ in range(steps):
+            st, _ = S.increment(model, st, dtau)
+        ini = float(np.sum(mat.degradation(st.phi, k) * st.psi_ini))
+        A_g = S.crack_area(model)
+        assert A_g == 12
+        gaps.append(S.toughness(model, st) - S.toughness_functional(model, st) - (ini - ini0) / A_g)
+    assert abs(gaps[0]) > 1.9 * abs(gaps[1]) > 3.6 * abs(gaps[2]), gaps
+    assert abs(gaps[2]) < 0.03 * abs(S.toughness_functional(model, st))
+
+
 def test_no_history_energy_balance_second_order():
     """Without history the damage equation g'(phi)(psi_o + psi_ini) + gamma_f' = 0 is the
     stationarity of Psi = E_mec + D + int g(phi) psi_ini, so the external work V T equals the
@@ -242,6 +305,47 @@ def test_no_history_energy_balance_second_order():
     # the gap is the quadrature error of the load curve: it vanishes at least linearly
     assert gaps[0] / gaps[1] > 1.9 and gaps[1] / gaps[2] > 1.9, gaps
     assert abs(gaps[2]) < 0.005 * works[2]
+
+
+def test_plate_one_voxel_thick_equals_plane_strain():
+    """A 3D plate one voxel thick (the RVEs of Sec. 5) with grains rotated about z only and the
+    load e_y (x) e_y is a plane-strain problem: xi_z = 0 leaves no zz fluctuation, cubic symmetry
+    about z decouples the anti-plane shears, and the cleavage tensor acts on an in-plane gradient.
+    So its increments equal those of the 2D model on the same grains, exactly up to rounding."""
+    import dataclasses
+    crack = synth.Crack(synth.CRACK_CTE, row=8, x0=0, length=4, phi_M=0.8)
+    m3 = synth.polycrystal_plate((32, 16), 8, 17, zener=4.0, beta=2.0, orientation="inplane", crack=crack)
+    m2 = dataclasses.replace(m3, n=(32, 16, 1), dim=2)
+    out = []
+    for m in (m3, m2):
+        model = S.Model(m, S.Params(ell=2.0, tol_stag=1e-11))
+        st = S.init_state(model)
+        for _ in range(2):
+            st, _ = S.increment(model, st, 0.4)
+        out.append((st, model))
+    (s3, m3_), (s2, _) = out
+    assert m3_.d == 3 and m3_.grid == (1, 16, 32)
+    for k in ("E", "Sigma", "D", "T", "Gamma", "Emec"):
+        a, b = s3.curve[-1][k], s2.curve[-1][k]
+        assert abs(a - b) <= 1e-9 * abs(b), (k, a, b)
+    assert np.max(np.abs(s3.phi.reshape(-1) - s2.phi.reshape(-1))) < 1e-9
+    # the anti-plane shears and the zz strain stay zero
+    assert np.max(np.abs(s3.eps[2])) < 1e-12 and np.max(np.abs(s3.eps[:, 2])) < 1e-12
+
+
+def test_laguerre_without_spread_is_voronoi():
+    """The power-weighted tessellation with equal radii is the plain periodic Voronoi one."""
+    from scipy.spatial import cKDTree
+    gid, seeds, radii, _ = synth.laguerre_ids((48, 32), 12, 3, sigma_size=0.0)
+    assert np.allclose(radii, radii[0])
+    tree = cKDTree(seeds, boxsize=[48, 32])
+    X, Y = np.meshgrid(np.arange(48) + 0.5, np.arange(32) + 0.5)
+    _, ref = tree.query(np.stack([X.ravel(), Y.ravel()], -1))
+    assert np.array_equal(gid.ravel(), ref)
+    # with spread, larger radii claim larger grains on average
+    gid, seeds, radii, _ = synth.laguerre_ids((256, 256), 60, 4, sigma_size=0.25)
+    size = np.bincount(gid.ravel(), minlength=60)
+    assert np.corrcoef(radii, size)[0, 1] > 0.5
 
 
 def test_converged_increments_zero_residuals():
