@@ -17,6 +17,12 @@ template <typename T> struct cplx_of;
 template <> struct cplx_of<double> { typedef double2 type; };
 template <> struct cplx_of<float> { typedef float2 type; };
 
+// Load of a field that no thread of the running kernel writes before reading it (each voxel is
+// read, then possibly rewritten, by the one thread that owns it). The read-only path lets the
+// compiler issue the loads of several voxels ahead of the stores of earlier ones, instead of
+// serialising every voxel behind a possibly aliasing store.
+template <typename T> __device__ __forceinline__ T ldro(const T *p) { return __ldg(p); }
+
 template <typename C> __device__ __forceinline__ C cmk(double re, double im) {
     C r; r.x = re; r.y = im; return r;
 }

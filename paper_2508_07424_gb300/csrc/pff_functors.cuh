@@ -24,8 +24,8 @@ struct MechBase {
     long long N;
     bool skip_if_done;
     __device__ __forceinline__ void stress(long long v, const T *u, T *out) const {
-        const T *C = Cm + (size_t)gid[v] * NS * NS;
-        const T gp = degr(phi[v], k);
+        const T *C = Cm + (size_t)ldro(gid + v) * NS * NS;
+        const T gp = degr(ldro(phi + v), k);
 #pragma unroll
         for (int a = 0; a < NS; ++a) {
             T s = 0;
@@ -377,12 +377,13 @@ struct ProCGCG : MechBase<T, NS> {
 #pragma unroll
         for (int a = 0; a < NS; ++a) {
             const size_t i = a * this->N + v;
-            const T pi = r[i] + be * p[i];
-            const T si = w[i] + be * s[i];
+            const T ri = ldro(r + i);
+            const T pi = ri + be * ldro(p + i);
+            const T si = ldro(w + i) + be * ldro(s + i);
             p[i] = pi;
             s[i] = si;
-            x[i] += al * pi;
-            rn[a] = r[i] - al * si;
+            x[i] = ldro(x + i) + al * pi;
+            rn[a] = ri - al * si;
             r[i] = rn[a];
         }
         this->stress(v, rn, out);
@@ -403,7 +404,7 @@ struct EpiCGCG {
         for (int a = 0; a < NS; ++a) {
             const size_t i = a * N + v;
             w[i] = val[a];
-            const double rv = (double)r[i];
+            const double rv = (double)ldro(r + i);
             acc[0] += rv * rv;
             acc[1] += (double)val[a] * rv;
         }
@@ -482,7 +483,7 @@ struct DmgCoef {
     T hmul;
     const T *H;
     __device__ __forceinline__ T a(long long v) const {
-        return acoef[gid[v]] + (hmul != (T)0 ? hmul * H[v] : (T)0);
+        return ldro(acoef + ldro(gid + v)) + (hmul != (T)0 ? hmul * ldro(H + v) : (T)0);
     }
 };
 
@@ -605,12 +606,12 @@ struct ProPCGCG {
     const Scal *scr;
     __device__ void eval(long long v, T *out, double *) const {
         const T al = (T)scr->alpha, be = (T)scr->beta;
-        const T pi = u[v] + be * p[v];
-        const T si = w[v] + be * s[v];
+        const T pi = ldro(u + v) + be * ldro(p + v);
+        const T si = ldro(w + v) + be * ldro(s + v);
+        const T rn = ldro(r + v) - al * si;
         p[v] = pi;
         s[v] = si;
-        x[v] += al * pi;
-        const T rn = r[v] - al * si;
+        x[v] = ldro(x + v) + al * pi;
         r[v] = rn;
         out[0] = rn;
     }
@@ -648,7 +649,7 @@ struct MidFluxU {  // [u, grad u] -> store u, K grad u
     T *u;
     __device__ void apply(long long v, const T *in, T *out) const {
         u[v] = in[0];
-        const T *K = Ktab + (size_t)gid[v] * 6;
+        const T *K = Ktab + (size_t)ldro(gid + v) * 6;
         if constexpr (D == 2) {
             out[0] = K[0] * in[1] + K[2] * in[2];
             out[1] = K[2] * in[1] + K[1] * in[2];
@@ -673,11 +674,11 @@ struct EpiPCGCG {
     const T *u, *r;
     T *w;
     __device__ void apply(long long v, const T *val, double *acc) const {
-        const T a = acoef[gid[v]] + (hmul != (T)0 ? hmul * H[v] : (T)0);
-        const T uv = u[v];
+        const T a = ldro(acoef + ldro(gid + v)) + (hmul != (T)0 ? hmul * ldro(H + v) : (T)0);
+        const T uv = ldro(u + v);
         const T wv = a * uv - val[0];
+        const double rv = (double)ldro(r + v);
         w[v] = wv;
-        const double rv = (double)r[v];
         acc[0] += rv * (double)uv;
         acc[1] += (double)wv * (double)uv;
         acc[2] += rv * rv;
@@ -720,7 +721,7 @@ struct MidFlux {  // grad v -> K grad v
     const T *Ktab;
     const int *gid;
     __device__ void apply(long long v, const T *in, T *out) const {
-        const T *K = Ktab + (size_t)gid[v] * 6;
+        const T *K = Ktab + (size_t)ldro(gid + v) * 6;
         if constexpr (D == 2) {
             out[0] = K[0] * in[0] + K[2] * in[1];
             out[1] = K[2] * in[0] + K[1] * in[1];

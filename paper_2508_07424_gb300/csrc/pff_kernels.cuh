@@ -77,7 +77,12 @@ __device__ __forceinline__ void load_packed(const Geom &g, const C *__restrict__
                                             C *line, int t, int TL) {
     const int nx = g.nx, nh2 = nx >> 1;
     const C *src = spec + (size_t)c * g.Nh + ((long long)z * g.ny + y0) * g.Px;
-    for (int k = t; k <= nh2; k += TL) {
+    // TL = nx / 4, so k = t, t + TL and (for t = 0 only) t + 2 TL = nx / 2; a fixed trip count
+    // lets the loads of all three be issued together
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int k = t + q * TL;
+        if (k > nh2) break;
         C Xa = src[k], Xb = src[g.Px + k];
         if (k == 0 || k == nh2) { Xa.y = 0; Xb.y = 0; }
         C Z;
@@ -215,8 +220,13 @@ __global__ void __launch_bounds__(512) k_axis(Geom g, int axis, const typename c
     const int other = blockIdx.y;
     const long long lstride = axis == 1 ? (long long)g.Px : (long long)g.Px * g.ny;
     const long long base = axis == 1 ? (long long)other * g.ny * g.Px : (long long)other * g.Px;
+    // blockDim.x = CW * L / 4: every loop over the tile's L * CW points takes exactly 4 steps,
+    // unrolled (fully up to 4 components, by 2 beyond, to stay within the register budget)
+    constexpr int UQ = NM <= 4 ? 4 : 2;
     const int nthreads = blockDim.x;
-    for (int i = threadIdx.x; i < L * CW; i += nthreads) {
+#pragma unroll UQ
+    for (int q = 0; q < 4; ++q) {
+        const int i = threadIdx.x + q * nthreads;
         const int pos = i / CW, cc = i - pos * CW;
 #pragma unroll
         for (int c = 0; c < NCI; ++c)
@@ -229,7 +239,9 @@ __global__ void __launch_bounds__(512) k_axis(Geom g, int axis, const typename c
         fft_lines<C, NM>(s, L, logL, NCI, 1, CW, tw, false);
     }
     if constexpr (MODE == AX_FWD_OP_INV) {
-        for (int i = threadIdx.x; i < L * CW; i += nthreads) {
+#pragma unroll UQ
+        for (int q = 0; q < 4; ++q) {
+            const int i = threadIdx.x + q * nthreads;
             const int pos = i / CW, cc = i - pos * CW;
             const int kx = kx0 + cc;
             const int ky = axis == 1 ? pos : other;
@@ -244,7 +256,9 @@ __global__ void __launch_bounds__(512) k_axis(Geom g, int axis, const typename c
         __syncthreads();
         fft_lines<C, NM>(s, L, logL, NCO, 1, CW, tw, true);
     }
-    for (int i = threadIdx.x; i < L * CW; i += nthreads) {
+#pragma unroll UQ
+    for (int q = 0; q < 4; ++q) {
+        const int i = threadIdx.x + q * nthreads;
         const int pos = i / CW, cc = i - pos * CW;
 #pragma unroll
         for (int c = 0; c < NOUT; ++c)
