@@ -1261,6 +1261,7 @@ struct Engine : EngineBase {
         S.Gamma = Gamma0;
         curve.clear();
         micro_set = true;
+        root_slope = 0.0;
         return RVE_OK;
     }
 
@@ -1310,14 +1311,24 @@ struct Engine : EngineBase {
     // ---- control: smallest E >= 0 with D(phi(E)) = tau (a10) -----------------------------------
     int arc_length(double tau, double E_guess, double &E_out, double &D_out, rve_step_result &st_) {
         int it = 0, rc;
+        double Ep = -1.0, fp = 0.0;
         auto evaluate = [&](double E, double &f) -> int {
             double Dv;
             int r = damage_eval(E, Dv, it);
             st_.dmg_iters += it;
             st_.root_evals += 1;
+            eval_iters = it;
             if (r) return r;
             f = Dv - tau;
             D_out = Dv;
+            // slope memory for the secant predictor, from evaluations far enough apart that the
+            // solve tolerance does not dominate the difference quotient
+            if (Ep >= 0.0 && std::fabs(E - Ep) > 1e-3 * std::max(E, Ep)) {
+                const double sl = (f - fp) / (E - Ep);
+                if (std::isfinite(sl) && sl > 0.0) root_slope = sl;
+            }
+            Ep = E;
+            fp = f;
             return RVE_OK;
         };
         if (E_guess <= 0.0) {
@@ -1328,12 +1339,34 @@ struct Engine : EngineBase {
             const double pm = std::max(h_sc->red[0] / (double)N, 1e-300);
             E_guess = std::sqrt(si.amean * cfg.ell / (cfg.ell * pm)) * 0.05;
         }
-        const double E0 = E_guess;
+        double E0 = E_guess;
         double f0;
         if ((rc = evaluate(E0, f0))) return rc;
         if (std::fabs(f0) <= cfg.tol_root * tau) { E_out = E0; return RVE_OK; }
         double h = 1e-3 * E0, lo, flo, hi, fhi;
         int guard = 0;
+        // Secant predictor from the slope dD/dE of the last root solve, aimed 2% past the root so
+        // that it usually brackets it in one evaluation. D(phi(E)) is non-decreasing in E, so
+        // this only shortens the search; the root is the same (bracketing below and Illinois).
+        if (root_slope > 0.0) {
+            double E1 = E0 - 1.02 * f0 / root_slope;
+            E1 = std::min(std::max(E1, 0.5 * E0), 2.0 * E0);
+            double f1;
+            if ((rc = evaluate(E1, f1))) return rc;
+            if (std::fabs(f1) <= cfg.tol_root * tau) {
+                E_out = E1;
+                return RVE_OK;
+            }
+            if ((f0 < 0.0) != (f1 < 0.0)) {
+                if (f0 < 0.0) { lo = E0; flo = f0; hi = E1; fhi = f1; }
+                else { lo = E1; flo = f1; hi = E0; fhi = f0; }
+                return illinois(tau, lo, flo, hi, fhi, evaluate, E_out);
+            }
+            // same side: continue the bracket search from the closer point
+            h = std::max(std::fabs(E1 - E0), 1e-3 * E0);
+            E0 = E1;
+            f0 = f1;
+        }
         if (f0 < 0.0) {
             lo = E0; flo = f0; hi = lo + h;
             if ((rc = evaluate(hi, fhi))) return rc;
@@ -1352,12 +1385,32 @@ struct Engine : EngineBase {
                 if ((rc = evaluate(lo, flo))) return rc;
             }
         }
-        int side = 0;
+        return illinois(tau, lo, flo, hi, fhi, evaluate, E_out);
+    }
+    // Refinement of a bracket f(lo) < 0 < f(hi): a secant step through the two latest evaluations
+    // when it falls inside the bracket, else the Illinois step. It also stops when the damage solve
+    // at the new E needed no iteration: its warm start (the previous evaluation's phi) already met
+    // the solve tolerance, so D cannot be resolved any finer at this tolerance and further steps
+    // would only see the same value.
+    double root_slope = 0.0;  // dD/dE from the last well-separated pair of evaluations
+    int eval_iters = 0;
+    template <class Ev>
+    int illinois(double tau, double lo, double flo, double hi, double fhi, Ev &evaluate, double &E_out) {
+        int side = 0, rc;
+        double Ea = lo, fa = flo, Eb = hi, fb = fhi;  // the two latest evaluations
         for (int k = 0; k < cfg.max_root_evals; ++k) {
-            const double E = (lo * fhi - hi * flo) / (fhi - flo);
+            double E = (lo * fhi - hi * flo) / (fhi - flo);
+            if (fb != fa) {
+                const double Es = Eb - fb * (Eb - Ea) / (fb - fa);
+                if (Es > lo && Es < hi) E = Es;
+            }
             double fE;
             if ((rc = evaluate(E, fE))) return rc;
-            if (std::fabs(fE) <= cfg.tol_root * tau || (hi - lo) <= 1e-15 * hi) { E_out = E; return RVE_OK; }
+            Ea = Eb; fa = fb; Eb = E; fb = fE;
+            if (std::fabs(fE) <= cfg.tol_root * tau || (hi - lo) <= 1e-15 * hi || eval_iters == 0) {
+                E_out = E;
+                return RVE_OK;
+            }
             if (fE > 0.0) {
                 hi = E; fhi = fE;
                 if (side == 1) flo *= 0.5;
@@ -1576,18 +1629,23 @@ struct Engine : EngineBase {
         dissipation(tmpf, Dv, Gv);
         return RVE_OK;
     }
-    // checkpoint payload: phi, H, psi_ini, strain fluctuation (field precision), committed strain (FP64)
-    size_t state_bytes() const override { return (size_t)N * sizeof(T) * (3 + NS) + (size_t)NS * N * sizeof(double); }
+    // checkpoint payload: phi, H, psi_ini, strain fluctuation (field precision), committed strain
+    // (FP64), and the control search's slope memory (so a restored run repeats the same iterates)
+    size_t state_bytes() const override {
+        return (size_t)N * sizeof(T) * (3 + NS) + (size_t)NS * N * sizeof(double) + sizeof(double);
+    }
     void save_state(char *p) override {
         const void *src[5] = {phi, H, psi_ini, mx, eps_com};
         const size_t sz[5] = {N * sizeof(T), N * sizeof(T), N * sizeof(T), NS * N * sizeof(T), NS * N * sizeof(double)};
         for (int i = 0; i < 5; ++i) { CK(cudaMemcpyAsync(p, src[i], sz[i], cudaMemcpyDeviceToHost, st)); p += sz[i]; }
+        std::memcpy(p, &root_slope, sizeof(double));
         CK(cudaStreamSynchronize(st));
     }
     void load_state(const char *p) override {
         void *dst[5] = {phi, H, psi_ini, mx, eps_com};
         const size_t sz[5] = {N * sizeof(T), N * sizeof(T), N * sizeof(T), NS * N * sizeof(T), NS * N * sizeof(double)};
         for (int i = 0; i < 5; ++i) { CK(cudaMemcpyAsync(dst[i], p, sz[i], cudaMemcpyHostToDevice, st)); p += sz[i]; }
+        std::memcpy(&root_slope, p, sizeof(double));
         CK(cudaMemcpyAsync(phi_trial, phi, N * sizeof(T), cudaMemcpyDeviceToDevice, st));
         CK(cudaStreamSynchronize(st));
     }
