@@ -164,6 +164,44 @@ def aggregate_over_ranks(ms, vu, world, device):
     return float(tmax[0].item()), float(t[1].item())
 
 
+def cufft_reference(torch, stream, g, w, precision):
+    """cuFFT (through torch.fft) timed beside the library's own transforms, as a reference only.
+
+    Ours: one equilibrium CG iteration, i.e. three fused passes (CG update + stress + x FFT; y FFT +
+    projection + inverse y FFT; inverse x FFT + CG vector + dot products), timed over a whole
+    solve from a zero fluctuation and divided by its iterations. cuFFT: the forward and inverse
+    real 2D FFT of the same three-component field alone, without the projection, the stress or
+    the CG arithmetic."""
+    import numpy as np
+    from paper_2508_07424_gb300 import capi
+    nx, ny = w.micro.n[0], w.micro.n[1]
+    g.set(capi.RVE_FIELD_FLUCT1, np.zeros((3, ny, nx)))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters = g.mech_solve()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ours_us = e0.elapsed_time(e1) * 1e3 / max(iters, 1)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    x = torch.randn(3, ny, nx, dtype=dt, device="cuda")
+    for _ in range(3):
+        torch.fft.irfft2(torch.fft.rfft2(x), s=(ny, nx))
+    reps = 50
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        y = torch.fft.irfft2(torch.fft.rfft2(x), s=(ny, nx))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    del y
+    return {"what": f"cuFFT rfft2 + irfft2 of a 3 x {ny} x {nx} {dt} field (torch.fft), no operator",
+            "cufft_us": e0.elapsed_time(e1) * 1e3 / reps,
+            "ours_us_per_mech_iteration": ours_us, "ours_iterations": iters,
+            "ours_what": "one equilibrium CG iteration: 3 fused passes incl. both FFTs, the projection, "
+                         "the stress, the CG updates and dot products (solve from zero / iterations)"}
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -287,6 +325,8 @@ def run_gpu(args):
         "roofline": roof,
         "e2e": e2e,
     }
+    if world == 1 and w.micro.dim == 2:
+        out["cufft_reference"] = cufft_reference(torch, stream, g, w, args.precision)
     if not args.no_cpu_baseline and world == 1 and args.workload == WORKLOAD:
         out["cpu_baseline"] = cpu_baseline(args, timed_steps=1)
     if args.precision == "fp32r" and world == 1 and args.workload == WORKLOAD:

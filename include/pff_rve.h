@@ -198,6 +198,16 @@ int rve_timing_get(rve_handle h, int kind, double *total_ms, long *launches, dou
 /* Number of kernels this handle launched so far. */
 long rve_launch_count(rve_handle h);
 
+/* Column tile widths (kx columns per CTA) of the y and z FFT passes that rve_create chose for this
+ * handle (*cw_z = 0 when the grid has no z pass). rve_create measures the admissible widths on the
+ * handle's own buffers once per device, grid, dimension and precision, and keeps the fastest in a
+ * process-wide table and a cache file of lines "<key> <cw_y> <cw_z>": $PFF_TILE_CACHE, else
+ * $XDG_CACHE_HOME/pff_gb300/tiles.txt, else ~/.cache/pff_gb300/tiles.txt (not written if none can
+ * be created). PFF_TILE_TUNE=0 keeps the built-in widths, PFF_TILE_CW=<y>,<z> forces admissible
+ * ones. Every column is transformed by the same code whatever the width, so results do not
+ * depend on the choice. Not from the paper: a tuning aid of this implementation. */
+int rve_tile_config(rve_handle h, int *cw_y, int *cw_z);
+
 int rve_destroy(rve_handle h);
 /* Message of a status; for RVE_ENOCONV, RVE_ENOROOT, RVE_EBREAKDOWN and RVE_ECUDA it is the
  * last failure recorded on the calling thread (which stage failed, with its numbers). */

@@ -75,6 +75,7 @@ _SIGS = {
     "rve_timing_enable": (C.c_int, [rve_handle, C.c_int]),
     "rve_timing_get": (C.c_int, [rve_handle, C.c_int, _dp, C.POINTER(C.c_long), _dp]),
     "rve_launch_count": (C.c_long, [rve_handle]),
+    "rve_tile_config": (C.c_int, [rve_handle, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "rve_destroy": (C.c_int, [rve_handle]),
     "rve_strerror": (C.c_char_p, [C.c_int]),
     "rve_footprint_bytes": (C.c_size_t, [C.POINTER(rve_config)]),

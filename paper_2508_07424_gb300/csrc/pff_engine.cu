@@ -12,14 +12,17 @@
 // keeps only scalar control: the bracketed Illinois search on E, the m x m Anderson
 // least-squares problem and the stopping tests.
 #include <cuda_runtime.h>
+#include <sys/stat.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <cstdlib>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -574,6 +577,67 @@ static void pinv_solve(int m, const double *Min, const double *b, double rcond, 
 }
 
 // ------------------------------------------------------------------------------------------------
+// Column-tile table of the autotuner: process-wide, backed by a text cache file of lines
+// "<key> <cw_y> <cw_z>" (the last line for a key wins).
+// ------------------------------------------------------------------------------------------------
+static std::mutex g_tile_mu;
+static std::mutex g_tune_mu;  // one measurement at a time, so concurrent handles do not skew it
+static std::map<std::string, std::pair<int, int>> g_tiles;
+static bool g_tiles_loaded = false;
+
+static std::string tile_cache_path() {
+    const char *p = std::getenv("PFF_TILE_CACHE");
+    if (p && *p) return p;
+    const char *x = std::getenv("XDG_CACHE_HOME");
+    std::string base;
+    if (x && *x) base = x;
+    else {
+        const char *h = std::getenv("HOME");
+        if (!h || !*h) return std::string();
+        base = std::string(h) + "/.cache";
+    }
+    return base + "/pff_gb300/tiles.txt";
+}
+
+static void tile_load_locked() {
+    if (g_tiles_loaded) return;
+    g_tiles_loaded = true;
+    const std::string path = tile_cache_path();
+    if (path.empty()) return;
+    FILE *f = std::fopen(path.c_str(), "r");
+    if (!f) return;
+    char key[512];
+    int y, z;
+    while (std::fscanf(f, "%511s %d %d", key, &y, &z) == 3) g_tiles[key] = {y, z};
+    std::fclose(f);
+}
+
+static bool tile_lookup(const std::string &key, int &y, int &z) {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    tile_load_locked();
+    auto it = g_tiles.find(key);
+    if (it == g_tiles.end()) return false;
+    y = it->second.first;
+    z = it->second.second;
+    return true;
+}
+
+static void tile_store(const std::string &key, int y, int z) {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    tile_load_locked();
+    g_tiles[key] = {y, z};
+    const std::string path = tile_cache_path();
+    if (path.empty()) return;
+    // create the directory chain; on failure the table stays in memory only
+    for (size_t i = 1; i < path.size(); ++i)
+        if (path[i] == '/') mkdir(path.substr(0, i).c_str(), 0755);
+    FILE *f = std::fopen(path.c_str(), "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d %d\n", key.c_str(), y, z);
+    std::fclose(f);
+}
+
+// ------------------------------------------------------------------------------------------------
 // The engine
 // ------------------------------------------------------------------------------------------------
 struct SetupInfo {
@@ -584,6 +648,7 @@ struct SetupInfo {
 struct EngineBase {
     rve_config cfg;
     Geom g;
+    int cw_y = 2, cw_z = 2;  // column tile widths of the y and z passes (autotuned)
     cudaStream_t st = nullptr;
     bool own_stream = false;
     int NS = 3, D = 2;
@@ -641,7 +706,6 @@ struct Engine : EngineBase {
     size_t ev_used = 0;
     double bytes_mech_axis = 0.0;
     std::map<const void *, size_t> smem_set;
-    int cw_y = 2, cw_z = 2;
     // CUDA graphs of one iteration chunk, keyed by (solver kind, solution buffer, coefficient
     // pointer): the kernels of a chunk take only pointers and the device scalar block, so one
     // captured graph is replayed for every chunk of every later solve of the same kind.
@@ -785,8 +849,9 @@ struct Engine : EngineBase {
         auto cw_of = [](int L) { int TL = L / 4; return std::max(2, std::min(16, 256 / std::max(TL, 1))); };
         cw_y = cw_of(g.ny);
         cw_z = g.nz > 1 ? cw_of(g.nz) : 2;
-        const int cw = std::max(cw_y, cw_z);
-        g.Px = ((g.nx / 2 + 1 + cw - 1) / cw) * cw;
+        // spectra and the kx table are sized for the widest column tile (16); the tile widths
+        // and the pitch Px actually used are settled by tune_tiles() below
+        g.Px = ((g.nx / 2 + 1 + 15) / 16) * 16;
         g.N = (long long)g.nx * g.ny * g.nz;
         g.Nh = (long long)g.Px * g.ny * g.nz;
         g.invN = 1.0 / (double)g.N;
@@ -847,8 +912,104 @@ struct Engine : EngineBase {
         const double s2 = 1.41421356237309504880;
         if (D == 2) { fM[0] = c.f[0]; fM[1] = c.f[1]; fM[2] = s2 * c.f[5]; }
         else { fM[0] = c.f[0]; fM[1] = c.f[1]; fM[2] = c.f[2]; fM[3] = s2 * c.f[3]; fM[4] = s2 * c.f[4]; fM[5] = s2 * c.f[5]; }
+        try {
+            tune_tiles();
+        } catch (...) {
+            release();
+            throw;
+        }
         // spectral bytes of one mechanics axis launch: read + write NS complex per spectral point
         bytes_mech_axis = 2.0 * NS * (double)g.Nh * sizeof(C);
+    }
+
+    // ---- column-tile autotuner -------------------------------------------------------------------
+    // The y (and z) passes take CW adjacent kx columns per CTA: wider tiles read longer contiguous
+    // runs of each spectral row, narrower ones give more CTAs. The best width depends on the grid,
+    // the dimension and the precision, so it is measured: every admissible (cw_y, cw_z) runs the
+    // mechanics projection pass on this handle's buffers, and the fastest is kept, in a process-
+    // wide table and in a cache file, keyed by device, grid, dimension and precision. Each column
+    // is transformed by the same code whatever its tile, so the choice does not change any result.
+    // Environment: PFF_TILE_TUNE=0 keeps the built-in widths; PFF_TILE_CW=<y>,<z> forces widths;
+    // PFF_TILE_CACHE=<file> names the cache (default $XDG_CACHE_HOME or ~/.cache, pff_gb300/tiles.txt).
+    void set_tiles(int cy, int cz) {
+        cw_y = cy;
+        cw_z = cz;
+        const int cw = std::max(cw_y, g.nz >= 4 ? cw_z : 1);
+        g.Px = ((g.nx / 2 + 1 + cw - 1) / cw) * cw;
+        g.Nh = (long long)g.Px * g.ny * g.nz;
+    }
+    std::vector<int> tile_candidates(int L) const {
+        std::vector<int> v;
+        const int TL = L / 4;
+        const int NM = std::max(NS, D);
+        for (int cw = 1; cw <= 16; cw *= 2) {
+            const size_t sm = (size_t)NM * cw * L * sizeof(C);
+            if (cw * TL >= 32 && cw * TL <= 512 && sm <= 200 * 1024) v.push_back(cw);
+        }
+        if (v.empty()) v.push_back(L >= 4 ? std::max(1, std::min(16, 128 / std::max(TL, 1))) : 2);
+        return v;
+    }
+    float time_tiles(int cy, int cz) {
+        set_tiles(cy, cz);
+        init_sc(sc, 0.0, 0);
+        cudaEvent_t a, b;
+        CK(cudaEventCreate(&a));
+        CK(cudaEventCreate(&b));
+        float best = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            CK(cudaEventRecord(a, st));
+            if (NS == 3) spectral<3, 3>(OpProj<C, 3>{false, xitab()}, sc);
+            else spectral<6, 6>(OpProj<C, 6>{false, xitab()}, sc);
+            CK(cudaEventRecord(b, st));
+            CK(cudaEventSynchronize(b));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, a, b));
+            if (rep > 0) best = std::min(best, ms);  // the first run warms up
+        }
+        CK(cudaEventDestroy(a));
+        CK(cudaEventDestroy(b));
+        return best;
+    }
+    std::string tile_key() const {
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        cudaDeviceProp pr;
+        CK(cudaGetDeviceProperties(&pr, dev));
+        char buf[256];
+        std::snprintf(buf, sizeof(buf), "%s|sm%d%d|d%d|%dx%dx%d|%s", pr.name, pr.major, pr.minor, D, g.nx, g.ny, g.nz,
+                      kSingle ? "fp32" : "fp64");
+        std::string k(buf);
+        for (char &ch : k)
+            if (ch == ' ') ch = '_';
+        return k;
+    }
+    void tune_tiles() {
+        const std::vector<int> cy = tile_candidates(g.ny);
+        const std::vector<int> cz = g.nz >= 4 ? tile_candidates(g.nz) : std::vector<int>{cw_z};
+        auto admissible = [&](int y, int z) {
+            return std::find(cy.begin(), cy.end(), y) != cy.end() && std::find(cz.begin(), cz.end(), z) != cz.end();
+        };
+        const char *force = std::getenv("PFF_TILE_CW");
+        if (force) {
+            int y = 0, z = 0;
+            if (std::sscanf(force, "%d,%d", &y, &z) == 2 && admissible(y, z)) { set_tiles(y, z); return; }
+        }
+        const char *tune = std::getenv("PFF_TILE_TUNE");
+        if (tune && std::string(tune) == "0") { set_tiles(cw_y, cw_z); return; }
+        const std::string key = tile_key();
+        int y = 0, z = 0;
+        if (tile_lookup(key, y, z) && admissible(y, z)) { set_tiles(y, z); return; }
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (tile_lookup(key, y, z) && admissible(y, z)) { set_tiles(y, z); return; }
+        float best = 1e30f;
+        int by = cw_y, bz = cw_z;
+        for (int yy : cy)
+            for (int zz : cz) {
+                const float ms = time_tiles(yy, zz);
+                if (ms < best) { best = ms; by = yy; bz = zz; }
+            }
+        set_tiles(by, bz);
+        tile_store(key, by, bz);
     }
 
     void release() {
@@ -1963,6 +2124,13 @@ int rve_timing_get(rve_handle h, int kind, double *total_ms, long *launches, dou
 }
 
 long rve_launch_count(rve_handle h) { return h ? h->e->launches : 0; }
+
+int rve_tile_config(rve_handle h, int *cw_y, int *cw_z) {
+    if (!h || !cw_y || !cw_z) return RVE_EINVAL;
+    *cw_y = h->e->cw_y;
+    *cw_z = h->e->g.nz >= 4 ? h->e->cw_z : 0;
+    return RVE_OK;
+}
 
 int rve_destroy(rve_handle h) {
     if (!h) return RVE_EINVAL;

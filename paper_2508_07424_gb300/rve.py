@@ -153,6 +153,11 @@ class Rve:
     def launches(self):
         return capi.lib().rve_launch_count(self.h)
 
+    def tiles(self):
+        y, z = C.c_int(), C.c_int()
+        capi.check(capi.lib().rve_tile_config(self.h, C.byref(y), C.byref(z)), "rve_tile_config")
+        return y.value, z.value
+
     def close(self):
         if self.h:
             capi.lib().rve_destroy(self.h)
