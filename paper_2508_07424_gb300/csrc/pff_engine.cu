@@ -1255,8 +1255,14 @@ struct Engine : EngineBase {
 
     // ---- damage (a6-a8) ------------------------------------------------------------------------
     // Generic FFT-preconditioned CG for  a v - div(K grad v) = rhs, warm-started from x.
+    // Damage (mode 0, 1) or enrichment (mode 2) solve. In damage mode *Dx_out receives D(x) of the
+    // solution: in FP32 from the final refinement pass, whose residual evaluation computed it from
+    // the converged x (no iteration followed); in FP64 from the residual identity of PwDmgEnergy.
+    // It is NaN when neither applies (the caller then evaluates D itself).
     template <int Dx> int pcg_t(int mode, double E, const DmgCoef<T> &co, const T *rhs, T rhs_scale, T *x,
-                                double tol, int maxit, double amean, double bbar, int &iters) {
+                                double tol, int maxit, double amean, double bbar, int &iters,
+                                double *Dx_out = nullptr) {
+        if (Dx_out) *Dx_out = NAN;
         ProDmgInit<T> pi{true, mode, E, psi1, psi_ini, H, Hcur, rhs, x, amean, bbar, (double)co.hmul, N};
         OpGrad<C, Dx> grad{true, xitab()};
         OpDiv<C, Dx> divo{true, xitab()};
@@ -1302,12 +1308,22 @@ struct Engine : EngineBase {
             if (!(h_sc->rr <= h_sc->tol2 * h_sc->scale2)) return fail(RVE_ENOCONV, "damage CG: iteration cap");
             if (!kSingle || h_sc->iters == 0) break;
         }
+        if (Dx_out && mode != 2) {
+            if (kSingle) {
+                if (h_sc->iters == 0) *Dx_out = h_sc->D;
+            } else {
+                init_sc(sc2, 0.0, 0);
+                pointwise(PwDmgEnergy<T>{false, x, dr, rhs, co.H, (double)rhs_scale, (double)co.hmul}, sc2);
+                read_sc(sc2);
+                *Dx_out = h_sc->D;
+            }
+        }
         return RVE_OK;
     }
     int pcg(int mode, double E, const DmgCoef<T> &co, const T *rhs, T rhs_scale, T *x, double tol, int maxit,
-            double amean, double bbar, int &iters) {
-        return D == 2 ? pcg_t<2>(mode, E, co, rhs, rhs_scale, x, tol, maxit, amean, bbar, iters)
-                      : pcg_t<3>(mode, E, co, rhs, rhs_scale, x, tol, maxit, amean, bbar, iters);
+            double amean, double bbar, int &iters, double *Dx_out = nullptr) {
+        return D == 2 ? pcg_t<2>(mode, E, co, rhs, rhs_scale, x, tol, maxit, amean, bbar, iters, Dx_out)
+                      : pcg_t<3>(mode, E, co, rhs, rhs_scale, x, tol, maxit, amean, bbar, iters, Dx_out);
     }
     DmgCoef<T> dmg_coef() const { return DmgCoef<T>{acoef, Ktab, gid, (T)2.0, Hcur}; }
 
@@ -1329,11 +1345,16 @@ struct Engine : EngineBase {
     // phi(E) into phi_trial (warm start = current phi_trial); returns D(phi(E)).
     int damage_eval(double E, double &Dv, int &iters) {
         const int mode = cfg.history ? 0 : 1;
+        double Dsol;
         int rc = pcg(mode, E, dmg_coef(), Hcur, (T)2.0, phi_trial, cfg.tol_dmg, cfg.max_dmg_iters, si.amean,
-                     si.bbar, iters);
+                     si.bbar, iters, &Dsol);
         if (rc) return rc;
-        double Gm;
-        dissipation(phi_trial, Dv, Gm);
+        if (std::isfinite(Dsol)) {
+            Dv = Dsol;
+        } else {
+            double Gm;
+            dissipation(phi_trial, Dv, Gm);
+        }
         return RVE_OK;
     }
 

@@ -733,10 +733,13 @@ struct MidFlux {  // grad v -> K grad v
     }
 };
 
-// r = rhs - (a x - div); reduces <r, r>.
+// r = rhs - (a x - div); reduces <r, r> and, in damage mode, the dissipation functional of x,
+// D(x) = sum Gc/(2l) x^2 + 1/2 x . (-div(Gc l A grad x)) (Eq. (CrackLenght_ani) by parts: the
+// spectral divergence is minus the adjoint of the spectral gradient), from the same operator
+// application.
 template <typename T>
 struct EpiDmgRes {
-    static constexpr int NR = 1;
+    static constexpr int NR = 2;
     bool skip_if_done;
     DmgCoef<T> co;
     const T *x;
@@ -744,18 +747,44 @@ struct EpiDmgRes {
     const T *rhs;
     T rhs_scale;
     __device__ void apply(long long v, const T *val, double *acc) const {
-        const T Lx = co.a(v) * x[v] - val[0];
+        const T xv = x[v];
+        const T Lx = co.a(v) * xv - val[0];
         const T rv = rhs_scale * rhs[v] - Lx;
         r[v] = rv;
         acc[0] += (double)rv * (double)rv;
+        const double a0 = (double)ldro(co.acoef + ldro(co.gid + v));  // Gc / l
+        acc[1] += 0.5 * (double)xv * (a0 * (double)xv - (double)val[0]);
     }
     struct Fin {
         Scal *sc;
         __device__ void operator()(const double *t) const {
+            sc->D = t[1];
             sc->rr = t[0]; sc->rr0 = t[0]; sc->iters = 0; sc->first = 1; sc->beta = 0.0; sc->alpha = 0.0;
             if (t[0] <= sc->tol2 * sc->scale2) sc->done = 1;
             if (!isfinite(t[0])) { sc->flag |= FLAG_NONFINITE; sc->done = 1; }
         }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+// Dissipation functional of a converged damage solve from its residual: with L x = b - r and
+// L = a0 + hmul H - div(K grad) (a0 = Gc / l, K = Gc l A), the identity
+// D(x) = sum a0/2 x^2 + 1/2 x . (-div(K grad x)) = 1/2 x . (b - r) - hmul/2 H x^2 holds exactly;
+// r is the solver's recursively updated residual.
+template <typename T>
+struct PwDmgEnergy {
+    static constexpr int NR = 1;
+    static constexpr bool MAXRED = false;
+    bool skip_if_done;
+    const T *x, *r, *rhs, *H;
+    double rhs_scale, hmul;
+    __device__ void apply(long long v, double *acc) const {
+        const double xv = (double)x[v];
+        acc[0] += 0.5 * xv * (rhs_scale * (double)rhs[v] - (double)r[v]) - 0.5 * hmul * (double)H[v] * xv * xv;
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const { sc->D = t[0]; }
     };
     __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
 };
