@@ -5,6 +5,7 @@ native code in csrc/pff_serve.cu; this module submits requests at their arrival 
 collects the results.
 """
 import ctypes as C
+import dataclasses
 import math
 import threading
 import time
@@ -86,3 +87,28 @@ def replay(server, requests, time_scale=1.0, **kw):
             out[r["id"]] = r
     th.join()
     return out, time.perf_counter() - t0
+
+
+def crack_position_sampling(server, w, positions, n_inc=None, timeout_s=600.0, **kw):
+    """Toughness of one RVE sampled over initial-crack positions (Sec. 3: the crack position can
+    bias the crack path, so the estimate is the minimum over positions).
+
+    positions: (row, x0) pairs for the crack of ``w.micro.crack`` (same kind, length, phi_M). Each
+    position is one request of the native server, so the solves run concurrently on the GPU.
+    Returns (minimum toughness over the positions that reached the fracture point, per-position
+    results in the order given). A position whose run fails or does not fracture within n_inc
+    increments keeps its status and fractured flag and is left out of the minimum."""
+    for i, (row, x0) in enumerate(positions):
+        cr = dataclasses.replace(w.micro.crack, row=int(row), x0=int(x0))
+        wi = dataclasses.replace(w, micro=dataclasses.replace(w.micro, crack=cr))
+        capi.check(server.submit(i, wi, n_inc or w.n_inc, **kw), "rve_server_submit")
+    out = {}
+    t_end = time.perf_counter() + timeout_s
+    while len(out) < len(positions):
+        if time.perf_counter() > t_end:
+            raise TimeoutError("crack_position_sampling: results missing after %.0f s" % timeout_s)
+        for r in server.wait(64, 0.5):
+            out[r["id"]] = r
+    res = [dict(out[i], row=int(positions[i][0]), x0=int(positions[i][1])) for i in range(len(positions))]
+    ok = [r["toughness"] for r in res if r["status"] == capi.RVE_OK and r["fractured"]]
+    return (min(ok) if ok else math.nan), res

@@ -3,7 +3,9 @@
 * each result is the same alone and in the mix (the kernels of one RVE do not depend on what
   else runs: same launch shapes, deterministic reductions), compared bit for bit;
 * admission honours the HBM budget (a budget that fits one request keeps one in flight);
-* a failing request is retired with its status and the others complete.
+* a failing request is retired with its status and the others complete;
+* crack-position sampling (Sec. 3): on a homogeneous periodic RVE every position gives the same
+  toughness (translation invariance), equal to a standalone run.
 """
 import numpy as np
 import pytest
@@ -80,3 +82,30 @@ def test_failing_request_is_retired_and_others_complete(mods):
     srv.close()
     assert out[1]["status"] == capi.RVE_EINVAL
     assert out[0]["status"] == capi.RVE_OK and out[2]["status"] == capi.RVE_OK
+
+
+def test_crack_position_sampling(mods):
+    capi, serve, Rve = mods
+    crack = synth.Crack(synth.CRACK_CTE, row=8, x0=0, length=4, phi_M=0.8)
+    w = synth.Workload(synth.homogeneous((16, 16), crack=crack), ell=2.0, n_inc=60)
+    w.dtau = 1.5 * 12 / 30
+    positions = [(8, 0), (3, 5), (12, 9), (0, 12)]
+    sv = serve.Server(max_inflight=4)
+    try:
+        gmin, res = serve.crack_position_sampling(sv, w, positions, tol_stag=1e-9)
+    finally:
+        sv.close()
+    assert all(r["status"] == capi.RVE_OK and r["fractured"] for r in res)
+    g = Rve.from_workload(w, tol_stag=1e-9)
+    for _ in range(60):
+        if g.step(w.dtau)["fractured"]:
+            break
+    G0 = g.toughness()
+    assert res[0]["toughness"] == G0                      # same request alone and in the server
+    # The other positions are periodic shifts of the same problem. They differ only by rounding,
+    # but the coalescence increment admits several solutions (the load is ~0 there), so G_F is
+    # compared at the level of that non-uniqueness, not of rounding.
+    for r in res:
+        assert abs(r["n_done"] - res[0]["n_done"]) <= 1
+        assert abs(r["toughness"] - G0) <= 0.02 * G0, (r["row"], r["x0"], r["toughness"], G0)
+    assert gmin == min(r["toughness"] for r in res)
