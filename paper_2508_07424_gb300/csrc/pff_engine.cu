@@ -1202,6 +1202,10 @@ struct Engine : EngineBase {
     // |P[sigma]| <= tol_mech |sigma|. The problem is positively homogeneous of degree one, so the
     // unit-load solution scales with E >= 0.
     T *epsk = nullptr, *mw = nullptr, *dw = nullptr;
+    // div(K grad x) of the damage field phi_trial as the last solve of the running control search
+    // left it (valid while ddiv_ok): the next solve of the same search starts without transforms
+    T *ddiv = nullptr;
+    bool ddiv_ok = false;
     int mech_solve_split(const T *phi_in, int &iters) {
         if (!epsk) epsk = alloc<T>((size_t)3 * N);
         ProSplitStress<T> pst{true, mx, phi_in, lamT, muT, gid, (T)cfg.k_res, {}, N};
@@ -1259,10 +1263,15 @@ struct Engine : EngineBase {
     // solution: in FP32 from the final refinement pass, whose residual evaluation computed it from
     // the converged x (no iteration followed); in FP64 from the residual identity of PwDmgEnergy.
     // It is NaN when neither applies (the caller then evaluates D itself).
+    // reuse: (damage mode) ddiv holds div(K grad x) for the current x; the first residual is then
+    // one pointwise pass. In damage mode ddiv is left valid for the returned x when *Dx_out is
+    // finite.
     template <int Dx> int pcg_t(int mode, double E, const DmgCoef<T> &co, const T *rhs, T rhs_scale, T *x,
                                 double tol, int maxit, double amean, double bbar, int &iters,
-                                double *Dx_out = nullptr) {
+                                double *Dx_out = nullptr, bool reuse = false) {
         if (Dx_out) *Dx_out = NAN;
+        if (!ddiv) ddiv = alloc<T>(N);
+        T *keep = mode != 2 ? ddiv : nullptr;
         ProDmgInit<T> pi{true, mode, E, psi1, psi_ini, H, Hcur, rhs, x, amean, bbar, (double)co.hmul, N};
         OpGrad<C, Dx> grad{true, xitab()};
         OpDiv<C, Dx> divo{true, xitab()};
@@ -1279,11 +1288,16 @@ struct Engine : EngineBase {
         for (int pass = 0; pass < passes; ++pass) {
             init_sc(sc, tol, std::max(1, maxit - iters));
             // r = rhs - L x (true residual), then the single-reduction iteration
-            x_fwd<1>(pi, sc);
-            spectral<1, Dx>(grad, sc);
-            x_mid<Dx>(flux, sc);
-            spectral<Dx, 1>(divo, sc);
-            x_inv<1>(EpiDmgRes<T>{true, co, x, dr, rhs, rhs_scale}, sc);
+            if (pass == 0 && reuse && mode != 2) {
+                pointwise(PwDmgInitKept<T>{false, mode, E, psi1, psi_ini, H, Hcur, co, x, ddiv, dr, amean, bbar, N},
+                          sc);
+            } else {
+                x_fwd<1>(pi, sc);
+                spectral<1, Dx>(grad, sc);
+                x_mid<Dx>(flux, sc);
+                spectral<Dx, 1>(divo, sc);
+                x_inv<1>(EpiDmgRes<T>{true, co, x, dr, rhs, rhs_scale, keep}, sc);
+            }
             auto iter_body = [&] {
                 x_fwd<1>(pdir, sc);
                 spectral<1, Dx + 1>(pgrad, sc);
@@ -1313,7 +1327,7 @@ struct Engine : EngineBase {
                 if (h_sc->iters == 0) *Dx_out = h_sc->D;
             } else {
                 init_sc(sc2, 0.0, 0);
-                pointwise(PwDmgEnergy<T>{false, x, dr, rhs, co.H, (double)rhs_scale, (double)co.hmul}, sc2);
+                pointwise(PwDmgEnergy<T>{false, co, x, dr, rhs, (double)rhs_scale, keep}, sc2);
                 read_sc(sc2);
                 *Dx_out = h_sc->D;
             }
@@ -1321,9 +1335,9 @@ struct Engine : EngineBase {
         return RVE_OK;
     }
     int pcg(int mode, double E, const DmgCoef<T> &co, const T *rhs, T rhs_scale, T *x, double tol, int maxit,
-            double amean, double bbar, int &iters, double *Dx_out = nullptr) {
-        return D == 2 ? pcg_t<2>(mode, E, co, rhs, rhs_scale, x, tol, maxit, amean, bbar, iters, Dx_out)
-                      : pcg_t<3>(mode, E, co, rhs, rhs_scale, x, tol, maxit, amean, bbar, iters, Dx_out);
+            double amean, double bbar, int &iters, double *Dx_out = nullptr, bool reuse = false) {
+        return D == 2 ? pcg_t<2>(mode, E, co, rhs, rhs_scale, x, tol, maxit, amean, bbar, iters, Dx_out, reuse)
+                      : pcg_t<3>(mode, E, co, rhs, rhs_scale, x, tol, maxit, amean, bbar, iters, Dx_out, reuse);
     }
     DmgCoef<T> dmg_coef() const { return DmgCoef<T>{acoef, Ktab, gid, (T)2.0, Hcur}; }
 
@@ -1346,9 +1360,12 @@ struct Engine : EngineBase {
     int damage_eval(double E, double &Dv, int &iters) {
         const int mode = cfg.history ? 0 : 1;
         double Dsol;
+        const bool reuse = ddiv_ok;
+        ddiv_ok = false;
         int rc = pcg(mode, E, dmg_coef(), Hcur, (T)2.0, phi_trial, cfg.tol_dmg, cfg.max_dmg_iters, si.amean,
-                     si.bbar, iters, &Dsol);
+                     si.bbar, iters, &Dsol, reuse);
         if (rc) return rc;
+        ddiv_ok = std::isfinite(Dsol);
         if (std::isfinite(Dsol)) {
             Dv = Dsol;
         } else {
@@ -1493,6 +1510,7 @@ struct Engine : EngineBase {
     // ---- control: smallest E >= 0 with D(phi(E)) = tau (a10) -----------------------------------
     int arc_length(double tau, double E_guess, double &E_out, double &D_out, rve_step_result &st_) {
         int it = 0, rc;
+        ddiv_ok = false;  // phi_trial was just reset to the staggered iterate
         double Ep = -1.0, fp = 0.0;
         auto evaluate = [&](double E, double &f) -> int {
             double Dv;
@@ -1803,7 +1821,10 @@ struct Engine : EngineBase {
         CK(cudaStreamSynchronize(st));
         return rc;
     }
-    int damage_eval_api(double E, double &Dv, int &iters) override { return damage_eval(E, Dv, iters); }
+    int damage_eval_api(double E, double &Dv, int &iters) override {
+        ddiv_ok = false;
+        return damage_eval(E, Dv, iters);
+    }
     int dissipation_host(const double *phi_host, double &Dv, double &Gv) override {
         CK(cudaMemcpyAsync(dtmp, phi_host, N * sizeof(double), cudaMemcpyHostToDevice, st));
         k_cast_copy<T><<<(int)((N + 255) / 256), 256, 0, st>>>(N, dtmp, tmpf);

@@ -529,6 +529,55 @@ struct ProDmgInit {
     __device__ Fin fin(Scal *sc) const { return Fin{sc, amean, bbar, hmul, 1.0 / (double)N}; }
 };
 
+// Start of a damage solve from an x whose div(K grad x) is kept (the previous solve of the same
+// control search ended at this x): the history H_E and the rhs as in ProDmgInit, then the true
+// residual r = b - (a x - div) and D(x) as in EpiDmgRes, without any transform.
+template <typename T>
+struct PwDmgInitKept {
+    static constexpr int NR = 4;
+    static constexpr bool MAXRED = false;
+    bool skip_if_done;
+    int mode;  // 0: with history, 1: without
+    double E;
+    const T *psi1, *psi_ini, *Hprev;
+    T *Hcur;
+    DmgCoef<T> co;  // co.H is Hcur
+    const T *x, *divx;
+    T *r;
+    double amean, bbar;
+    long long N;
+    __device__ void apply(long long v, double *acc) const {
+        const T drive = (T)(E * E) * ldro(psi1 + v) + ldro(psi_ini + v);
+        const T hp = ldro(Hprev + v);
+        const T H = (mode == 0) ? (drive > hp ? drive : hp) : drive;
+        Hcur[v] = H;
+        const T xv = ldro(x + v), dv = ldro(divx + v);
+        const T a0 = ldro(co.acoef + ldro(co.gid + v));
+        const T Lx = (a0 + co.hmul * H) * xv - dv;
+        const T b = (T)2 * H;
+        const T rv = b - Lx;
+        r[v] = rv;
+        acc[0] += (double)H;
+        acc[1] += (double)b * (double)b;
+        acc[2] += (double)rv * (double)rv;
+        acc[3] += 0.5 * (double)xv * ((double)a0 * (double)xv - (double)dv);
+    }
+    struct Fin {
+        Scal *sc;
+        double amean, bbar, hmul, invN;
+        __device__ void operator()(const double *t) const {
+            sc->abar = amean + hmul * t[0] * invN;
+            sc->bbar = bbar;
+            sc->scale2 = t[1];
+            sc->D = t[3];
+            sc->rr = t[2]; sc->rr0 = t[2]; sc->iters = 0; sc->first = 1; sc->beta = 0.0; sc->alpha = 0.0;
+            if (t[2] <= sc->tol2 * sc->scale2) sc->done = 1;
+            if (!isfinite(t[2])) { sc->flag |= FLAG_NONFINITE; sc->done = 1; }
+        }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc, amean, bbar, (double)co.hmul, 1.0 / (double)N}; }
+};
+
 template <typename T>
 struct ProField {
     static constexpr int NR = 0;
@@ -746,11 +795,13 @@ struct EpiDmgRes {
     T *r;
     const T *rhs;
     T rhs_scale;
+    T *divx;  // optional: keeps div(K grad x) for a later solve from the same x
     __device__ void apply(long long v, const T *val, double *acc) const {
         const T xv = x[v];
         const T Lx = co.a(v) * xv - val[0];
         const T rv = rhs_scale * rhs[v] - Lx;
         r[v] = rv;
+        if (divx) divx[v] = val[0];
         acc[0] += (double)rv * (double)rv;
         const double a0 = (double)ldro(co.acoef + ldro(co.gid + v));  // Gc / l
         acc[1] += 0.5 * (double)xv * (a0 * (double)xv - (double)val[0]);
@@ -776,11 +827,15 @@ struct PwDmgEnergy {
     static constexpr int NR = 1;
     static constexpr bool MAXRED = false;
     bool skip_if_done;
-    const T *x, *r, *rhs, *H;
-    double rhs_scale, hmul;
+    DmgCoef<T> co;
+    const T *x, *r, *rhs;
+    double rhs_scale;
+    T *divx;  // optional: div(K grad x) = a x - (b - r), kept for a later solve from the same x
     __device__ void apply(long long v, double *acc) const {
         const double xv = (double)x[v];
-        acc[0] += 0.5 * xv * (rhs_scale * (double)rhs[v] - (double)r[v]) - 0.5 * hmul * (double)H[v] * xv * xv;
+        const double b_r = rhs_scale * (double)rhs[v] - (double)r[v];
+        acc[0] += 0.5 * xv * b_r - 0.5 * (double)co.hmul * (double)co.H[v] * xv * xv;
+        if (divx) divx[v] = (T)((double)co.a(v) * xv - b_r);
     }
     struct Fin {
         Scal *sc;
