@@ -138,7 +138,8 @@ typedef struct {
 void rve_config_default(rve_config *cfg);
 
 /* Allocate the device state of one RVE. cfg is copied. Errors: RVE_EINVAL (grid not a power of
- * two in [4, 1024], dim/nz mismatch, ell <= 0, unsupported precision), RVE_ENOMEM, RVE_ECUDA. */
+ * two in [4, 1024], dim/nz mismatch, grid too small for one warp per x-pass CTA, i.e.
+ * (nx/4) * min(128/(nx/4), ny*nz/2) < 32, ell <= 0, unsupported precision), RVE_ENOMEM, RVE_ECUDA. */
 int rve_create(const rve_config *cfg, rve_handle *out);
 
 /* Upload the microstructure and build the per-grain tables: rotated stiffness C^r (Eq. (Crot)),
@@ -257,7 +258,8 @@ int rve_server_destroy(rve_server s);
  *   stream: cudaStream_t or NULL. The call is asynchronous on that stream.
  * Scratch: one fixed 8 MiB __device__ array inside the library, held by every GPU that loads it
  * until the process exits; nothing is allocated. Grids whose spectra and partial sums do not fit
- * (e.g. 2D above 512 x 512, 3D above 32^3) return RVE_EINVAL with a message on stderr.
+ * (e.g. 2D above 512 x 512, 3D above 32^3) return RVE_EINVAL with a message on stderr; so do
+ * grids too small for one warp per x-pass CTA (as for rve_create).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress), so
  * make that first call before any stream capture. All calls share the array: calls that
  * overlap on the GPU (different streams, different host threads) race and must be ordered by

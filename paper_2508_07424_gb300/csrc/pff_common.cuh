@@ -126,17 +126,31 @@ __device__ __forceinline__ void reduce_finalize(double (&v)[NR], double *partial
     __syncthreads();
     if (!last) return;
     __threadfence();
+    // Last block: every thread combines the partials b = tid, tid + blockDim, ... in that order
+    // (L2 loads, independent of each other, so they are all in flight at once), then the block
+    // combines the threads in a fixed tree. The order is fixed, so the result is deterministic.
+    double loc[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) loc[k] = use_max ? -1e300 : 0.0;
+    for (unsigned b = threadIdx.x; b < nb; b += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            const double p = __ldcg(partials + (size_t)k * nb + b);
+            loc[k] = use_max ? fmax(loc[k], p) : loc[k] + p;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const double t = use_max ? warp_max(loc[k]) : warp_sum(loc[k]);
+        if (lane == 0) sh[k][wid] = t;
+    }
+    __syncthreads();
     if (wid == 0) {
         double tot[NR];
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
-            double t = use_max ? -1e300 : 0.0;
-            for (unsigned b = lane; b < nb; b += 32) {
-                double p = ((volatile double *)partials)[(size_t)k * nb + b];
-                t = use_max ? fmax(t, p) : t + p;
-            }
-            t = use_max ? warp_max(t) : warp_sum(t);
-            tot[k] = t;
+            double t = (lane < nw) ? sh[k][lane] : (use_max ? -1e300 : 0.0);
+            tot[k] = use_max ? warp_max(t) : warp_sum(t);
         }
         if (lane == 0) {
             fin(tot);

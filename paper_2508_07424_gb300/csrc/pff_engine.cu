@@ -1990,6 +1990,16 @@ int rve_create(const rve_config *cfg, rve_handle *out) {
     if (cfg->dim == 2 && cfg->n[2] != 1) return RVE_EINVAL;
     if (cfg->dim == 3 && cfg->n[2] != 1 && !pow2_in(cfg->n[2], 4, 1024)) return RVE_EINVAL;
     if ((long long)cfg->n[0] * cfg->n[1] * cfg->n[2] > (1LL << 24)) return RVE_EINVAL;
+    {
+        // the x passes reduce with full-warp shuffles: their CTAs need at least one whole warp
+        const int TL = cfg->n[0] / 4;
+        const long long pairs = (long long)cfg->n[1] * cfg->n[2] / 2;
+        const long long RP = std::min<long long>(std::max(1, 128 / TL), pairs);
+        if (RP * TL < 32) {
+            g_last_error = "grid too small: the x passes need (nx/4) * min(128/(nx/4), ny*nz/2) >= 32";
+            return RVE_EINVAL;
+        }
+    }
     if (!(cfg->ell > 0) || cfg->k_res < 0 || cfg->anderson_m < 0 || cfg->anderson_m > 5) return RVE_EINVAL;
     if (cfg->split != RVE_SPLIT_NONE && cfg->split != RVE_SPLIT_SPECTRAL) return RVE_EINVAL;
     if (cfg->split == RVE_SPLIT_SPECTRAL && cfg->dim != 2) return RVE_EINVAL;  // split: plane strain only

@@ -103,6 +103,7 @@ extern "C" int rve_dissipation_noalloc(int dim, const int n[3], double ell, int 
     if (RP > pairs) RP = (int)pairs;
     const int xthreads = RP * TL;
     const int xblocks = (int)(pairs / RP);
+    if (xthreads < 32) return RVE_EINVAL;  // the x passes reduce with full-warp shuffles
 
     // scratch layout; reject grids whose requirement exceeds the static array
     Layout lay;

@@ -42,7 +42,10 @@ def test_create_rejects_bad_sizes_without_touching_the_gpu(lib):
     from paper_2508_07424_gb300 import capi
     from paper_2508_07424_gb300.rve import make_config
     bad = [dict(dim=2, n=(48, 64, 1)), dict(dim=2, n=(64, 64, 2)), dict(dim=3, n=(64, 64, 2)),
-           dict(dim=4, n=(64, 64, 1)), dict(dim=2, n=(2048, 64, 1)), dict(dim=3, n=(512, 512, 512))]
+           dict(dim=4, n=(64, 64, 1)), dict(dim=2, n=(2048, 64, 1)), dict(dim=3, n=(512, 512, 512)),
+           # too small for one warp per x-pass CTA: (nx/4) * min(128/(nx/4), ny*nz/2) < 32
+           dict(dim=2, n=(4, 4, 1)), dict(dim=2, n=(8, 8, 1)), dict(dim=2, n=(16, 8, 1)),
+           dict(dim=3, n=(8, 4, 1))]
     for b in bad:
         cfg = make_config(b["dim"], b["n"], 2.0)
         h = capi.rve_handle()
