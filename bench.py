@@ -217,7 +217,8 @@ def run_gpu(args):
         return run_batched_3d(args, torch, stream)
     w = make_workload(rank, args.precision, args.workload)
     tol = solver_tols(args.precision)
-    g = Rve.from_workload(w, stream=stream.cuda_stream, **tol)
+    solver = capi.RVE_SOLVER_NEWTON if args.solver == "newton" else capi.RVE_SOLVER_STAGGERED
+    g = Rve.from_workload(w, stream=stream.cuda_stream, solver=solver, **tol)
     N = g.nvox
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -293,7 +294,12 @@ def run_gpu(args):
     if w.micro.dim == 3:
         bytes_l, flops_l = float("nan"), float("nan")
     avg_s = ax_ms * 1e-3 / max(ax_n, 1)
-    if args.precision == "fp64":
+    if ax_n == 0:
+        # the Newton solver applies the projection inside its Jacobian, not in the timed CG pass
+        roof = {"kernel": "k_axis (mechanics: FFT_y + projection + inverse FFT_y)", "bound": None,
+                "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
+                "note": "not timed: no equilibrium CG pass runs with this solver", "launches": 0}
+    elif args.precision == "fp64":
         peak = 152 * 2 * 2 * 2.07e9 / 1e12   # FP64: 2 DFMA/clk/SM (1.26 TFLOP/s), see the design doc
         roof = {"kernel": "k_axis (mechanics: FFT_y + projection + inverse FFT_y)", "bound": "alu",
                 "timing": "CUDA events per launch over 3 instrumented increments after the timed region",
@@ -302,21 +308,26 @@ def run_gpu(args):
                 "traffic": None, "avg_launch_us": avg_s * 1e6, "launches": ax_n}
     else:
         peak = pk["hbm_gbs"]
+        # DRAM bytes of one launch from an ncu capture of this kernel on this workload
+        # (profiles/k_axis_opproj_fibre512_fp32.md); other workloads have no capture
+        traffic = 3197952 if (args.workload == WORKLOAD and w.micro.n[0] == 512) else None
         roof = {"kernel": "k_axis (mechanics: FFT_y + projection + inverse FFT_y)", "bound": "hbm",
                 "timing": "CUDA events per launch over 3 instrumented increments after the timed region",
                 "achieved": bytes_l / avg_s / 1e9, "peak": peak, "unit": "GB/s",
-                "frac": bytes_l / avg_s / 1e9 / peak, "peak_source": src, "traffic": None,
-                "avg_launch_us": avg_s * 1e6, "launches": ax_n}
+                "frac": bytes_l / avg_s / 1e9 / peak, "peak_source": src, "traffic": traffic,
+                "algorithmic_bytes": bytes_l, "avg_launch_us": avg_s * 1e6, "launches": ax_n}
     out = {
         "metric": f"FFT-PFF voxel-updates/s ({args.workload} increments)",
         "value": tot_vu / (tot_ms * 1e-3),
         "unit": "voxel-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": tot_ms / args.steps,
+        "voxel_increments_per_s": N * args.steps * world / (tot_ms * 1e-3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32",
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": workload_desc(args.workload), "precision": args.precision,
+                   "solver": args.solver,
                    "step": "one dissipation increment", "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas{world}"},
         "increments": [{k: r[k] for k in ("n", "mech_iters", "dmg_iters", "stag_iters", "root_evals")} for r in results],
@@ -567,6 +578,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=list(WORKLOADS))
+    ap.add_argument("--solver", default="staggered", choices=["staggered", "newton"],
+                    help="increment solver: staggered fixed point (default) or the monolithic Newton of Sec. 4.1")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-inc", type=int, default=10)
     args = ap.parse_args()

@@ -81,7 +81,19 @@ typedef struct {
     int anderson_m;        /* Anderson memory of the staggered iteration (0 = plain) */
     double fracture_ratio; /* fracture point F: Sigma^F <= ratio * max Sigma (Sec. 4.2) */
     void *stream;          /* cudaStream_t to run on; NULL: the handle creates its own */
+    int solver;            /* RVE_SOLVER_STAGGERED (default): staggered fixed point with the control
+                              root search; RVE_SOLVER_NEWTON: the monolithic Newton-Raphson of Sec. 4.1
+                              (Eqs. (schemeSys)-(relax)) with BiCGSTAB, FP64 only (RVE_EINVAL with
+                              RVE_FP32R: BiCGSTAB on the coupled single-precision system broke down
+                              before its tolerance), no split; the first increment
+                              (E = 0) is staggered, since at E = 0 the Jacobian does not couple E to
+                              the damage. Newton steps are capped by min(max_stag_iters, 50); in
+                              rve_step_result, stag_iters counts Newton steps and mech_iters
+                              BiCGSTAB iterations. Both solve the same equations (same converged
+                              state). */
 } rve_config;
+
+enum { RVE_SOLVER_STAGGERED = 0, RVE_SOLVER_NEWTON = 1 };
 
 /* Microstructure (Sec. 2.2, Sec. 4.3). All pointers are host pointers, copied. */
 typedef struct {

@@ -10,6 +10,7 @@ RVE_SPLIT_NONE, RVE_SPLIT_SPECTRAL = 0, 1
 RVE_STEP_STAGNATED, RVE_STEP_CUTBACK, RVE_STEP_UNCONVERGED = 1, 2, 4
 RVE_FP64, RVE_FP32R = 0, 1
 RVE_CRACK_NONE, RVE_CRACK_CTE, RVE_CRACK_CPFE = 0, 1, 2
+RVE_SOLVER_STAGGERED, RVE_SOLVER_NEWTON = 0, 1
 (RVE_FIELD_PHI, RVE_FIELD_H, RVE_FIELD_PSI_INI, RVE_FIELD_EPS, RVE_FIELD_SIGMA, RVE_FIELD_FLUCT1,
  RVE_FIELD_PSI1, RVE_FIELD_PHI_TRIAL) = range(8)
 
@@ -20,7 +21,7 @@ class rve_config(C.Structure):
                 ("tol_mech", C.c_double), ("tol_dmg", C.c_double), ("tol_root", C.c_double),
                 ("tol_stag", C.c_double), ("max_mech_iters", C.c_int), ("max_dmg_iters", C.c_int),
                 ("max_root_evals", C.c_int), ("max_stag_iters", C.c_int), ("anderson_m", C.c_int),
-                ("fracture_ratio", C.c_double), ("stream", C.c_void_p)]
+                ("fracture_ratio", C.c_double), ("stream", C.c_void_p), ("solver", C.c_int)]
 
 
 class rve_micro(C.Structure):

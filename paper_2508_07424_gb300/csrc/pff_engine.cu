@@ -31,6 +31,7 @@
 #include "pff_common.cuh"
 #include "pff_functors.cuh"
 #include "pff_kernels.cuh"
+#include "pff_newton.cuh"
 
 using namespace pff;
 
@@ -382,6 +383,17 @@ struct PwAAMix {  // phi = G_K - sum_a gamma_a (G_{a+1} - G_a)
     __device__ Fin fin(Scal *) const { return Fin{}; }
 };
 
+// Committed total strain of a Newton increment: eps = E f + e (Mandel, FP64).
+struct F6 {
+    double f[6];
+};
+template <typename T>
+__global__ void k_nr_total_strain(long long N, int NS, const T *e, double E, F6 f, double *eps) {
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= N) return;
+    for (int a = 0; a < NS; ++a) eps[a * N + v] = E * f.f[a] + (double)e[a * N + v];
+}
+
 // Tensor-component conversion (xx, yy, zz, yz, xz, xy) <-> Mandel, and stress evaluation.
 template <typename T>
 __global__ void k_mandel_to_tensor(long long N, int dim, const T *src, double scale, const double *f, double *dst) {
@@ -694,7 +706,7 @@ struct Engine : EngineBase {
     double *eps_it = nullptr, *eps_com = nullptr, *xh = nullptr, *gh = nullptr, *dtmp = nullptr;
     C *spec = nullptr;
     std::map<int, C *> tw;
-    Scal *sc = nullptr, *sc2 = nullptr, *h_sc = nullptr;
+    Scal *sc = nullptr, *sc2 = nullptr, *h_sc = nullptr, *sc3 = nullptr;
     double *partials = nullptr;
     int G = 0;
     bool iso_damage = true;
@@ -1628,7 +1640,269 @@ struct Engine : EngineBase {
     // coalescence), the increment is replaced by two of half the dissipation, recursively up to
     // four levels; each sub-increment is committed as its own point of the load curve.
     bool stag_failed = false, accept_unconverged = false;
-    int step(double dtau, rve_step_result *out) override { return step_cut(dtau, out, 0); }
+    int step(double dtau, rve_step_result *out) override {
+        // the Newton scheme needs E > 0 (psi_o is quadratic in E, so at E = 0 the Jacobian has no
+        // coupling from E to the damage): the first increment is taken by the staggered solver
+        if (cfg.solver == RVE_SOLVER_NEWTON && S.E > 0.0) return step_newton(dtau, out);
+        return step_cut(dtau, out, 0);
+    }
+
+    // ---- monolithic Newton-Raphson increment (Sec. 4.1) ------------------------------------------
+    // Newton on (e, phi, E) with BiCGSTAB for J dq = -R (Eqs. (schemeSys), (aniSystem_CrackLength),
+    // (aniCrackLength_linearization)), right-preconditioned on the damage block by the FFT
+    // Helmholtz inverse; the shadow residual is a fixed hash vector (with the right-hand side as
+    // shadow, the first step divides by ~0: J has no E-E entry). Relaxation of Eq. (relax),
+    // stopping test of Eq. (errors_crack) as in the staggered solver. The BiCGSTAB scalars live
+    // on the host (one read per reduction); the E components of the vectors too.
+    T *nrbuf = nullptr;
+    template <class F> void pointwise_n(const F &f, Scal *s, long long n) {
+        const int th = 256;
+        long long bl = (n + th - 1) / th;
+        if (bl > 1184) bl = 1184;
+        k_pointwise<F><<<(int)bl, th, 0, st>>>(n, f, partials, s);
+        CK(cudaGetLastError());
+        ++launches;
+    }
+    template <int NSx> NRPoint<T, NSx> nr_point(const T *e, const T *ph, double E) const {
+        NRPoint<T, NSx> q{Cm, gid, e, ph, E, {}, cfg.k_res, N};
+        for (int a = 0; a < NSx; ++a) q.f[a] = fM[a];
+        return q;
+    }
+    // v -> J v (vectors [e | phi] plus the E component); returns J3 (the E component of J v)
+    template <int NSx, int Dx> double nr_apply(const NRPoint<T, NSx> &q, const T *vin, double vE, T *vout) {
+        init_sc(sc2, 0.0, 0);
+        x_fwd<NSx>(ProNRMech<T, NSx>{false, q, vin, vin + (size_t)NSx * N, vE}, sc2);
+        spectral<NSx, NSx>(OpProj<C, NSx>{false, xitab()}, sc2);
+        x_inv<NSx>(EpiNRStore<T, NSx>{false, vout, 1.0, N}, sc2);
+        x_fwd<1>(ProField<T>{false, vin + (size_t)NSx * N}, sc2);
+        spectral<1, Dx>(OpGrad<C, Dx>{false, xitab()}, sc2);
+        x_mid<Dx>(MidFlux<T, Dx>{false, Ktab, gid}, sc2);
+        spectral<Dx, 1>(OpDiv<C, Dx>{false, xitab()}, sc2);
+        x_inv<1>(EpiNRDmg<T, NSx>{false, q, acoef, psi_ini, H, cfg.history, vin, vin + (size_t)NSx * N, vE,
+                                  vout + (size_t)NSx * N},
+                 sc2);
+        read_sc(sc2);
+        return h_sc->red[0];
+    }
+    // b = -R at q; returns -R3 and the norms of R1, R2 and their scales, D and sum H
+    struct NRRes { double mR3, nR1, nR2, s1, s2, D, Hsum; };
+    template <int NSx, int Dx> NRRes nr_residual(const NRPoint<T, NSx> &q, double tau, T *b) {
+        init_sc(sc2, 0.0, 0);
+        x_fwd<NSx>(ProNRMech<T, NSx>{false, q, nullptr, nullptr, 0.0}, sc2);
+        spectral<NSx, NSx>(OpProj<C, NSx>{false, xitab()}, sc2);
+        x_inv<NSx>(EpiNRStore<T, NSx>{false, b, -1.0, N}, sc2);
+        x_fwd<1>(ProField<T>{false, q.phi}, sc2);
+        spectral<1, Dx>(OpGrad<C, Dx>{false, xitab()}, sc2);
+        x_mid<Dx>(MidFlux<T, Dx>{false, Ktab, gid}, sc2);
+        spectral<Dx, 1>(OpDiv<C, Dx>{false, xitab()}, sc2);
+        x_inv<1>(EpiNRDmg<T, NSx>{false, q, acoef, psi_ini, H, cfg.history, nullptr, nullptr, 0.0,
+                                  b + (size_t)NSx * N},
+                 sc2);
+        read_sc(sc2);
+        NRRes r;
+        r.nR1 = std::sqrt(h_sc->rr);
+        r.s1 = std::sqrt(h_sc->scale2);
+        r.nR2 = std::sqrt(h_sc->red[0]);
+        r.s2 = std::sqrt(h_sc->red[1]);
+        r.D = h_sc->red[2];
+        r.Hsum = h_sc->red[3];
+        r.mR3 = -(r.D - tau);
+        return r;
+    }
+    // right preconditioner: identity on e and E, (abar + bbar |xi~|^2)^-1 on phi (abar, bbar in sc3)
+    void nr_precond(const T *in, T *out) {
+        CK(cudaMemcpyAsync(out, in, sizeof(T) * NS * N, cudaMemcpyDeviceToDevice, st));
+        x_fwd<1>(ProField<T>{false, in + (size_t)NS * N}, sc3);
+        spectral<1, 1>(OpPrec<C>{false, sc3, xitab()}, sc3);
+        x_inv<1>(EpiStore<T>{false, out + (size_t)NS * N}, sc3);
+    }
+    double nr_dot(const T *a, const T *b, long long n) {
+        init_sc(sc2, 0.0, 0);
+        pointwise_n(PwVDot<T>{false, a, b, nullptr, nullptr}, sc2, n);
+        read_sc(sc2);
+        return h_sc->red[0];
+    }
+    void nr_dot2(const T *a, const T *b, const T *c, const T *d, long long n, double &ab, double &cd) {
+        init_sc(sc2, 0.0, 0);
+        pointwise_n(PwVDot<T>{false, a, b, c, d}, sc2, n);
+        read_sc(sc2);
+        ab = h_sc->red[0];
+        cd = h_sc->red[1];
+    }
+    void nr_comb(T *out, const T *a, double ca, const T *b, double cb, const T *c, double cc, long long n) {
+        pointwise_n(PwVComb<T>{false, out, a, b, c, ca, cb, cc}, sc2, n);
+    }
+    template <int NSx, int Dx>
+    int nr_bicgstab(const NRPoint<T, NSx> &q, const T *b, double bE, double tol, int maxit, T *x, double &xE,
+                    int &its) {
+        // work vectors: slots 3..10 of nrbuf (0: iterate, 1: right-hand side, 2: solution)
+        const long long n = (long long)(NSx + 1) * N;
+        T *r = nrbuf + 3 * n, *rh = nrbuf + 4 * n, *p = nrbuf + 5 * n, *v = nrbuf + 6 * n, *s = nrbuf + 7 * n,
+          *t = nrbuf + 8 * n, *ph = nrbuf + 9 * n, *sh = nrbuf + 10 * n;
+        CK(cudaMemsetAsync(x, 0, sizeof(T) * n, st));
+        CK(cudaMemcpyAsync(r, b, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemsetAsync(p, 0, sizeof(T) * n, st));
+        CK(cudaMemsetAsync(v, 0, sizeof(T) * n, st));
+        pointwise_n(PwVHash<T>{false, rh}, sc2, n);
+        double rE = bE, rhE = 1.0, pE = 0.0, vE = 0.0;
+        xE = 0.0;
+        const double nb = std::sqrt(nr_dot(b, b, n) + bE * bE);
+        its = 0;
+        if (!(nb > 0.0)) return RVE_OK;
+        double rho = 1.0, alpha = 1.0, omega = 1.0, nr_last = nb;
+        // a breakdown (rho or omega vanishing) with the residual already small keeps x: in FP32 the
+        // recurrences reach the rounding floor of the vectors before a strict tolerance
+        auto breakdown = [&]() { return nr_last <= 1e-3 * nb ? RVE_OK : fail(RVE_EBREAKDOWN, "Newton: BiCGSTAB breakdown"); };
+        for (int it = 1; it <= maxit; ++it) {
+            its = it;
+            const double rho_new = nr_dot(rh, r, n) + rhE * rE;
+            if (rho_new == 0.0 || !std::isfinite(rho_new)) return breakdown();
+            const double beta = (rho_new / rho) * (alpha / omega);
+            nr_comb(p, r, 1.0, p, beta, v, -beta * omega, n);  // p = r + beta (p - omega v)
+            pE = rE + beta * (pE - omega * vE);
+            nr_precond(p, ph);
+            const double phE = pE;
+            vE = nr_apply<NSx, Dx>(q, ph, phE, v);
+            alpha = rho_new / (nr_dot(rh, v, n) + rhE * vE);
+            nr_comb(s, r, 1.0, v, -alpha, nullptr, 0.0, n);
+            const double sE = rE - alpha * vE;
+            const double ns = std::sqrt(nr_dot(s, s, n) + sE * sE);
+            if (ns <= tol * nb) {
+                nr_comb(x, x, 1.0, ph, alpha, nullptr, 0.0, n);
+                xE += alpha * phE;
+                return RVE_OK;
+            }
+            nr_precond(s, sh);
+            const double shE = sE;
+            const double tE = nr_apply<NSx, Dx>(q, sh, shE, t);
+            double ts, tt;
+            nr_dot2(t, s, t, t, n, ts, tt);
+            ts += tE * sE;
+            tt += tE * tE;
+            omega = ts / tt;
+            if (!std::isfinite(omega) || omega == 0.0) {
+                if (ns <= 1e-3 * nb) {
+                    nr_comb(x, x, 1.0, ph, alpha, nullptr, 0.0, n);
+                    xE += alpha * phE;
+                    return RVE_OK;
+                }
+                return breakdown();
+            }
+            nr_comb(x, x, 1.0, ph, alpha, sh, omega, n);
+            xE += alpha * phE + omega * shE;
+            nr_comb(r, s, 1.0, t, -omega, nullptr, 0.0, n);
+            rE = sE - omega * tE;
+            const double nr = std::sqrt(nr_dot(r, r, n) + rE * rE);
+            if (!std::isfinite(nr)) return fail(RVE_EBREAKDOWN, "Newton: BiCGSTAB non-finite residual");
+            nr_last = nr;
+            if (nr <= tol * nb) return RVE_OK;
+            rho = rho_new;
+        }
+        return fail(RVE_ENOCONV, "Newton: BiCGSTAB iteration cap");
+    }
+    int step_newton(double dtau, rve_step_result *out) {
+        if (!micro_set) return RVE_ESTATE;
+        if (!(dtau > 0.0)) return RVE_EINVAL;
+        return NS == 3 ? (D == 2 ? step_newton_t<3, 2>(dtau, out) : step_newton_t<3, 3>(dtau, out))
+                       : step_newton_t<6, 3>(dtau, out);
+    }
+    template <int NSx, int Dx> int step_newton_t(double dtau, rve_step_result *out) {
+        const long long n = (long long)(NSx + 1) * N;
+        if (!nrbuf) nrbuf = alloc<T>((size_t)11 * n);
+        if (!sc3) sc3 = alloc<Scal>(1);
+        T *qv = nrbuf, *b = nrbuf + n, *dq = nrbuf + 2 * n;  // iterate [e | phi], -R, Newton step
+        rve_step_result r{};
+        const double tau = S.tau + dtau;
+        double E = S.E;
+        // q_0 = q^n: e = E x (x the committed unit-load fluctuation), phi^n
+        nr_comb(qv, mx, E, nullptr, 0.0, nullptr, 0.0, (long long)NSx * N);
+        CK(cudaMemcpyAsync(qv + (size_t)NSx * N, phi, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+        const double alpha = S.Sigma_max > 0.0 ? std::max(0.3, S.Sigma / S.Sigma_max) : 1.0;
+        const double tol_floor = 1e-14;
+        double err = 1e300, Dv = 0.0;
+        int newton = 0, lin = 0;
+        bool converged = false;
+        for (int k = 0; k < cfg.max_stag_iters && k < 50; ++k) {
+            const NRPoint<T, NSx> q = nr_point<NSx>(qv, qv + (size_t)NSx * N, E);
+            const NRRes R = nr_residual<NSx, Dx>(q, tau, b);
+            if (!std::isfinite(R.nR1) || !std::isfinite(R.nR2) || !std::isfinite(R.D))
+                return fail(RVE_EBREAKDOWN, "Newton: non-finite residual");
+            init_sc(sc3, 0.0, 0, si.amean + 2.0 * R.Hsum / (double)N, si.bbar);
+            const double tol_lin = std::max(tol_floor, std::min(1e-4, 0.01 * err));
+            int its = 0;
+            double dE = 0.0;
+            int rc = nr_bicgstab<NSx, Dx>(q, b, R.mR3, tol_lin, 4000, dq, dE, its);
+            if (rc) return rc;
+            lin += its;
+            ++newton;
+            nr_comb(qv, qv, 1.0, dq, alpha, nullptr, 0.0, n);  // q += alpha dq
+            E += alpha * dE;
+            // Eq. (errors_crack) at the new point: strain change (degraded energy norm), damage
+            // change, control
+            const NRPoint<T, NSx> q1 = nr_point<NSx>(qv, qv + (size_t)NSx * N, E);
+            nr_comb(dq, dq, alpha, nullptr, 0.0, nullptr, 0.0, n);  // the applied step
+            init_sc(sc2, 0.0, 0);
+            pointwise(PwNRErr<T, NSx>{false, q1, dq, dq + (size_t)NSx * N, alpha * dE}, sc2);
+            read_sc(sc2);
+            const double e1 = std::sqrt(std::max(h_sc->red[0], 0.0)) / std::max(std::sqrt(std::max(h_sc->red[1], 0.0)), 1e-300);
+            const double e2 = std::sqrt(h_sc->red[2]) / std::max(std::sqrt(h_sc->red[3]), 1e-300);
+            double Gm;
+            dissipation(qv + (size_t)NSx * N, Dv, Gm);
+            err = std::max(std::max(e1, e2), std::fabs(Dv - tau) / tau);
+            if (err < cfg.tol_stag) { converged = true; break; }
+        }
+        r.stag_iters = newton;
+        r.mech_iters = lin;  // BiCGSTAB iterations (each applies the coupled Jacobian twice)
+        r.stag_err = err;
+        if (!converged) {
+            char buf[160];
+            std::snprintf(buf, sizeof(buf), "Newton-Raphson: %d steps, error %.3e (tol %.1e) at increment %d", newton,
+                          err, cfg.tol_stag, S.n + 1);
+            g_last_error = buf;
+            if (out) *out = r;
+            return RVE_ENOCONV;
+        }
+        // commit: phi, strain, unit-load fluctuation, history, Sigma, E_mec, T
+        const NRPoint<T, NSx> q = nr_point<NSx>(qv, qv + (size_t)NSx * N, E);
+        CK(cudaMemcpyAsync(phi, qv + (size_t)NSx * N, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(phi_trial, phi, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+        pointwise(PwNRHistory<T, NSx>{false, q, psi_ini, H, cfg.history, Hcur}, sc2);
+        CK(cudaMemcpyAsync(H, Hcur, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+        nr_comb(mx, qv, 1.0 / E, nullptr, 0.0, nullptr, 0.0, (long long)NSx * N);
+        F6 f6{};
+        for (int a = 0; a < NSx; ++a) f6.f[a] = fM[a];
+        k_nr_total_strain<T><<<(int)((N + 255) / 256), 256, 0, st>>>(N, NSx, qv, E, f6, eps_com);
+        CK(cudaGetLastError());
+        ++launches;
+        PwPsi1<T, NSx> ps{false, Cm, mx, gid, psi1, {}, N};
+        for (int a = 0; a < NSx; ++a) ps.f[a] = (T)fM[a];
+        pointwise(ps, sc2);
+        init_sc(sc2, 0, 0);
+        PwCommit<T, NSx> pc{false, Cm, mx, phi, psi1, gid, {}, E, cfg.k_res, N};
+        for (int a = 0; a < NSx; ++a) pc.f[a] = fM[a];
+        pointwise(pc, sc2);
+        read_sc(sc2);
+        const double Sigma = h_sc->red[4] / (double)N;
+        const double Emec = h_sc->red[5];
+        double Dc, Gc_;
+        dissipation(phi, Dc, Gc_);
+        const double dT = 0.5 * (Sigma + S.Sigma) * (E - S.E), dG = Gc_ - S.Gamma;
+        r.G_inst = dG != 0.0 ? (double)N * dT / dG : NAN;
+        S.T += dT;
+        S.D = Dc;
+        S.Gamma = Gc_;
+        S.Sigma = Sigma;
+        S.Sigma_max = std::max(S.Sigma_max, Sigma);
+        S.E = E;
+        S.tau = tau;
+        S.n += 1;
+        S.fractured = (S.Sigma_max > 0.0 && Sigma <= cfg.fracture_ratio * S.Sigma_max) ? 1 : 0;
+        r.n = S.n; r.E = E; r.Sigma = Sigma; r.D = Dc; r.Emec = Emec; r.T = S.T; r.Gamma = Gc_; r.tau = tau;
+        r.fractured = S.fractured;
+        curve.push_back(r);
+        if (out) *out = r;
+        return RVE_OK;
+    }
     int step_cut(double dtau, rve_step_result *out, int depth) {
         rve_step_result a{};
         accept_unconverged = false;
@@ -1978,6 +2252,7 @@ void rve_config_default(rve_config *c) {
     c->anderson_m = 5;
     c->fracture_ratio = 0.01;
     c->stream = nullptr;
+    c->solver = RVE_SOLVER_STAGGERED;
 }
 
 static bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
@@ -2003,6 +2278,13 @@ int rve_create(const rve_config *cfg, rve_handle *out) {
     if (!(cfg->ell > 0) || cfg->k_res < 0 || cfg->anderson_m < 0 || cfg->anderson_m > 5) return RVE_EINVAL;
     if (cfg->split != RVE_SPLIT_NONE && cfg->split != RVE_SPLIT_SPECTRAL) return RVE_EINVAL;
     if (cfg->split == RVE_SPLIT_SPECTRAL && cfg->dim != 2) return RVE_EINVAL;  // split: plane strain only
+    if (cfg->solver != RVE_SOLVER_STAGGERED && cfg->solver != RVE_SOLVER_NEWTON) return RVE_EINVAL;
+    if (cfg->solver == RVE_SOLVER_NEWTON && cfg->split != RVE_SPLIT_NONE) return RVE_EINVAL;  // not linearised
+    if (cfg->solver == RVE_SOLVER_NEWTON && cfg->precision != RVE_FP64) {
+        // BiCGSTAB on the coupled single-precision system broke down before its tolerance
+        g_last_error = "the Newton solver runs in FP64 only";
+        return RVE_EINVAL;
+    }
     if (cfg->precision != RVE_FP64 && cfg->precision != RVE_FP32R) return RVE_EINVAL;
     GUARD_BEGIN
     auto *h = new rve_s();

@@ -147,6 +147,7 @@ size_t rve_footprint_bytes(const rve_config *c) {
              + N * 6 * 8                        // host transfer staging
              + N * NS * 2 * w * 2;              // half spectra (padded)
     if (c->split == RVE_SPLIT_SPECTRAL) b += N * 3 * w;
+    if (c->solver == RVE_SOLVER_NEWTON) b += N * (NS + 1) * 11 * w;  // Newton iterate and BiCGSTAB vectors
     return b + (size_t)(24 * 65536) * 8 + (4u << 20);  // reduction partials, tables, slack
 }
 

@@ -50,6 +50,14 @@ def test_create_rejects_bad_sizes_without_touching_the_gpu(lib):
         cfg = make_config(b["dim"], b["n"], 2.0)
         h = capi.rve_handle()
         assert lib.rve_create(C.byref(cfg), C.byref(h)) == capi.RVE_EINVAL, b
+    # the Newton solver: FP64 only, no split
+    for kw in (dict(precision=capi.RVE_FP32R), dict(split=capi.RVE_SPLIT_SPECTRAL), dict(solver_bad=True)):
+        cfg = make_config(2, (64, 64, 1), 2.0, solver=capi.RVE_SOLVER_NEWTON,
+                          **{k: v for k, v in kw.items() if k != "solver_bad"})
+        if "solver_bad" in kw:
+            cfg.solver = 7
+        h = capi.rve_handle()
+        assert lib.rve_create(C.byref(cfg), C.byref(h)) == capi.RVE_EINVAL, kw
     cfg = make_config(2, (64, 64, 1), -1.0)
     h = capi.rve_handle()
     assert lib.rve_create(C.byref(cfg), C.byref(h)) == capi.RVE_EINVAL
