@@ -1117,11 +1117,22 @@ struct Engine : EngineBase {
         ++launches;
         if (e2) CK(cudaEventRecord(e2, st));
     }
+    // Grid of the pointwise kernels. Those that reduce pay a fixed per-CTA cost (block reduction,
+    // fence, atomic ticket), which dominated at one voxel per thread; they run 2 CTAs per SM with
+    // a grid-stride loop instead. The others take one voxel per thread up to 1184 CTAs.
+    int num_sms = 0;
+    template <class F> long long pw_blocks(long long n) {
+        if (!num_sms) {
+            int dev = 0;
+            CK(cudaGetDevice(&dev));
+            CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+        }
+        long long bl = (n + 255) / 256;
+        const long long cap = F::NR > 0 ? 2LL * num_sms : 1184;
+        return bl > cap ? cap : bl;
+    }
     template <class F> void pointwise(const F &f, Scal *s) {
-        const int th = 256;
-        long long bl = (N + th - 1) / th;
-        if (bl > 1184) bl = 1184;
-        k_pointwise<F><<<(int)bl, th, 0, st>>>(N, f, partials, s);
+        k_pointwise<F><<<(int)pw_blocks<F>(N), 256, 0, st>>>(N, f, partials, s);
         CK(cudaGetLastError());
         ++launches;
     }
@@ -1656,10 +1667,7 @@ struct Engine : EngineBase {
     // on the host (one read per reduction); the E components of the vectors too.
     T *nrbuf = nullptr;
     template <class F> void pointwise_n(const F &f, Scal *s, long long n) {
-        const int th = 256;
-        long long bl = (n + th - 1) / th;
-        if (bl > 1184) bl = 1184;
-        k_pointwise<F><<<(int)bl, th, 0, st>>>(n, f, partials, s);
+        k_pointwise<F><<<(int)pw_blocks<F>(n), 256, 0, st>>>(n, f, partials, s);
         CK(cudaGetLastError());
         ++launches;
     }
