@@ -283,7 +283,8 @@ def run_gpu(args):
         e2e = {"value": evu / et * world, "unit": "voxel-updates/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": e_steps,
                "what": "set_microstructure from host arrays + enriched-crack setup + one increment + D2H of "
-                       "result and damage field, per step"}
+                       "result and damage field, per step; the increment is the first of a fresh RVE, whose "
+                       "iteration mix differs from increments 4.. of the device-timed run"}
         ge.close()
 
     if rank != 0:
