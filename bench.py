@@ -112,6 +112,9 @@ WORKLOADS = {
     "polycrystal_plate_256": "256x128x1 polycrystal plate (six strain components), 60 Laguerre grains with lognormal "
                              "size spread 0.25, SO(3)-uniform orientations, cubic C1111:C1122=24:8 with Zener 4, "
                              "cleavage beta=2, l=2, CTE crack 26 voxels, dtau=1.5*A_g/200",
+    "polycrystal_3d_128": "128^3 periodic Voronoi polycrystal, 150 grains, cubic C11=1 C12=0.6 C44=0.5 with "
+                          "SO(3)-uniform orientations, lognormal Gc (sigma 0.3), l=2, through CTE crack 13 voxels, "
+                          "dtau=1.5*<Gc>*A_g/100 (the largest RVE of the batched 3D mix, alone)",
     "batched_3d_polycrystals": "16 periodic Voronoi 3D polycrystals, grids drawn from {32,64,128}^3, 50-200 grains, "
                                "cubic C11=1 C12=0.6 C44=0.5 with SO(3)-uniform orientations, lognormal Gc (sigma 0.3), "
                                "l=2, through CTE crack 0.1 n, dtau=1.5*<Gc>*A_g/100; run as 16 concurrent streams",
@@ -126,6 +129,8 @@ def make_workload(rank, precision, name=WORKLOAD):
         w = synth.polycrystal_1024(seed=2 + rank)
     elif name == "polycrystal_plate_256":
         w = synth.polycrystal_plate_256(seed=5 + rank)
+    elif name == "polycrystal_3d_128":
+        w = synth.polycrystal_3d(128, 150, 9 + rank)
     else:
         w = synth.fibre_composite_512(seed=1 + rank)
     w.precision = precision
@@ -139,15 +144,29 @@ def solver_tols(precision):
 
 
 # ---- algorithmic work of the dominant kernel ----------------------------------------------------
-def axis_kernel_model(nx, ny, ns, word):
-    """Mechanics spectral pass (forward FFT along y, projection, inverse FFT) on one launch:
-    bytes = read + write of ns complex values per half-spectrum point; flops = 2 transforms x
-    5 log2(ny) per complex point and component + ~40 per point for the projection."""
+def axis_kernel_model(nx, ny, ns, word, nz=1):
+    """One launch of the mechanics column pass: bytes = read + write of ns complex values per
+    half-spectrum point. 2D (and plates one voxel thick): y FFT, projection, inverse y FFT in one
+    launch; flops = 2 transforms x 5 log2(ny) per complex point and component + ~40 per point.
+    3D: three launches per projection (y, z with the projection, y), each moving the same bytes;
+    flops are not modelled there (NaN)."""
     import math
-    npts = (nx // 2 + 1) * ny
+    npts = (nx // 2 + 1) * ny * nz
     bytes_ = 2.0 * ns * npts * 2 * word
-    flops = npts * ns * 2 * 5 * math.log2(ny) + 40.0 * npts
+    flops = npts * ns * 2 * 5 * math.log2(ny) + 40.0 * npts if nz == 1 else float("nan")
     return bytes_, flops
+
+
+def _finite(obj):
+    """JSON has no NaN / Infinity: report such values as null."""
+    import math
+    if isinstance(obj, float):
+        return obj if math.isfinite(obj) else None
+    if isinstance(obj, dict):
+        return {k: _finite(v) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return [_finite(v) for v in obj]
+    return obj
 
 
 def aggregate_over_ranks(ms, vu, world, device):
@@ -291,9 +310,8 @@ def run_gpu(args):
         return None
     pk, src = peaks()
     word = 8 if args.precision == "fp64" else 4
-    bytes_l, flops_l = axis_kernel_model(w.micro.n[0], w.micro.n[1], 3, word)
-    if w.micro.dim == 3:
-        bytes_l, flops_l = float("nan"), float("nan")
+    bytes_l, flops_l = axis_kernel_model(w.micro.n[0], w.micro.n[1], 3 if w.micro.dim == 2 else 6, word,
+                                         w.micro.n[2])
     avg_s = ax_ms * 1e-3 / max(ax_n, 1)
     if ax_n == 0:
         # the Newton solver applies the projection inside its Jacobian, not in the timed CG pass
@@ -301,7 +319,7 @@ def run_gpu(args):
                 "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
                 "note": "not timed: no equilibrium CG pass runs with this solver", "launches": 0}
     elif args.precision == "fp64":
-        peak = 152 * 2 * 2 * 2.07e9 / 1e12   # FP64: 2 DFMA/clk/SM (1.26 TFLOP/s), see the design doc
+        peak = 152 * 2 * 2 * 2.07e9 / 1e12   # FP64: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz = 1.26 TFLOP/s
         roof = {"kernel": "k_axis (mechanics: FFT_y + projection + inverse FFT_y)", "bound": "alu",
                 "timing": "CUDA events per launch over 3 instrumented increments after the timed region",
                 "achieved": flops_l / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
@@ -589,7 +607,7 @@ def main():
         args.precision = "fp64" if args.workload == "homogeneous_plate_64" else "fp32r"
     out = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if out is not None:
-        print(json.dumps(out))
+        print(json.dumps(_finite(out)))
 
 
 if __name__ == "__main__":
