@@ -204,7 +204,11 @@ int rve_save(rve_handle h, void *buf, size_t *len);
 int rve_load(rve_handle h, const void *buf, size_t len);
 
 /* Per-kernel device timing (CUDA events around every launch of the named kernel class while
- * enabled). kind: 0 = mechanics spectral pass (the y/z-axis FFT + projection kernel). */
+ * enabled). kind: 0 = the mechanics projection pass (y/z FFT + projection + inverse); 1 = every
+ * column pass (k_axis: the mechanics projection and the damage gradient, divergence and
+ * preconditioner passes). bytes_per_launch is the average of the half-spectrum components read
+ * and written per launch. While timing is on, solves launch one iteration at a time (no graphs,
+ * no launch past convergence). */
 int rve_timing_enable(rve_handle h, int on);
 int rve_timing_get(rve_handle h, int kind, double *total_ms, long *launches, double *bytes_per_launch);
 

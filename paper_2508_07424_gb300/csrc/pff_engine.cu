@@ -683,7 +683,7 @@ struct EngineBase {
     virtual void save_state(char *p) = 0;
     virtual void load_state(const char *p) = 0;
     virtual void timing_reset() = 0;
-    virtual void timing_get(double &ms, long &n, double &bytes) = 0;
+    virtual void timing_get(int kind, double &ms, long &n, double &bytes) = 0;
     double crack_area() const { return (double)(g.nx - crack_len_) * (D == 3 ? g.nz : 1); }
     double toughness_value() const { return (double)N / crack_area() * (S.T - 0.5 * S.Sigma * S.E); }
     double toughness_functional_value() const { return (S.D - S.tau0) / crack_area(); }
@@ -716,6 +716,7 @@ struct Engine : EngineBase {
     // timing
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
     size_t ev_used = 0;
+    std::vector<std::pair<int, double>> ev_meta;  // (mechanics projection pass?, bytes moved)
     double bytes_mech_axis = 0.0;
     std::map<const void *, size_t> smem_set;
     // CUDA graphs of one iteration chunk, keyed by (solver kind, solution buffer, coefficient
@@ -1103,12 +1104,17 @@ struct Engine : EngineBase {
         auto k = k_axis<T, NCI, NCO, MODE, Op>;
         prep_smem(k, sm);
         cudaEvent_t e1 = nullptr, e2 = nullptr;
-        if (timed && timing) {
+        if (timing) {
+            // every column pass is timed; `timed` marks the mechanics projection pass. Bytes: the
+            // NCI components read and the components written, over the whole half spectrum.
             if (ev_used == ev_pool.size()) {
                 cudaEvent_t a, b;
                 CK(cudaEventCreate(&a)); CK(cudaEventCreate(&b));
                 ev_pool.push_back({a, b});
             }
+            const int nout = MODE == AX_FWD_OP_INV ? NCO : NCI;
+            if (ev_meta.size() < ev_pool.size()) ev_meta.resize(ev_pool.size());
+            ev_meta[ev_used] = {timed ? 1 : 0, (double)(NCI + nout) * (double)g.Nh * sizeof(C)};
             e1 = ev_pool[ev_used].first; e2 = ev_pool[ev_used].second; ++ev_used;
             CK(cudaEventRecord(e1, st));
         }
@@ -1179,7 +1185,7 @@ struct Engine : EngineBase {
         // from the equilibrium residual recomputed from the current strain, until that true
         // residual meets the tolerance (a pass that needs no iteration).
         const int passes = kSingle ? 8 : 1;
-        const int chunk = 8;
+        const int chunk = timing ? 1 : 8;  // timed runs launch no iteration past convergence
         iters = 0;
         for (int pass = 0; pass < passes; ++pass) {
             if (pass > 0) {
@@ -1306,7 +1312,7 @@ struct Engine : EngineBase {
         EpiPCGCG<T> ew{true, co.acoef, gid, co.hmul, co.H, dz, dr, dw};
         // FP64: one PCG pass; FP32: passes restarted from the true residual (see mech_solve_t).
         const int passes = kSingle ? 8 : 1;
-        const int chunk = 4;
+        const int chunk = timing ? 1 : 4;
         iters = 0;
         for (int pass = 0; pass < passes; ++pass) {
             init_sc(sc, tol, std::max(1, maxit - iters));
@@ -2135,17 +2141,21 @@ struct Engine : EngineBase {
         CK(cudaStreamSynchronize(st));
     }
     void timing_reset() override { ev_used = 0; }
-    void timing_get(double &ms, long &n, double &bytes) override {
+    void timing_get(int kind, double &ms, long &n, double &bytes) override {
         CK(cudaStreamSynchronize(st));
-        double tot = 0.0;
+        double tot = 0.0, by = 0.0;
+        long cnt = 0;
         for (size_t i = 0; i < ev_used; ++i) {
+            if (kind == 0 && !ev_meta[i].first) continue;
             float t = 0.f;
             CK(cudaEventElapsedTime(&t, ev_pool[i].first, ev_pool[i].second));
             tot += t;
+            by += ev_meta[i].second;
+            ++cnt;
         }
         ms = tot;
-        n = (long)ev_used;
-        bytes = bytes_mech_axis;
+        n = cnt;
+        bytes = cnt ? by / (double)cnt : 0.0;
     }
 
     // ---- field access --------------------------------------------------------------------------
@@ -2453,11 +2463,11 @@ int rve_timing_enable(rve_handle h, int on) {
 }
 
 int rve_timing_get(rve_handle h, int kind, double *total_ms, long *launches, double *bytes_per_launch) {
-    if (!h || kind != 0) return RVE_EINVAL;
+    if (!h || (kind != 0 && kind != 1)) return RVE_EINVAL;
     GUARD_BEGIN
     double ms = 0.0, b = 0.0;
     long n = 0;
-    h->e->timing_get(ms, n, b);
+    h->e->timing_get(kind, ms, n, b);
     if (total_ms) *total_ms = ms;
     if (launches) *launches = n;
     if (bytes_per_launch) *bytes_per_launch = b;

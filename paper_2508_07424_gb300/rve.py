@@ -142,12 +142,12 @@ class Rve:
     def load(self, blob):
         capi.check(capi.lib().rve_load(self.h, blob, len(blob)), "rve_load")
 
-    def timing(self, on=None):
+    def timing(self, on=None, kind=0):
         if on is not None:
             capi.check(capi.lib().rve_timing_enable(self.h, int(on)), "rve_timing_enable")
             return None
         ms, n, b = C.c_double(), C.c_long(), C.c_double()
-        capi.check(capi.lib().rve_timing_get(self.h, 0, C.byref(ms), C.byref(n), C.byref(b)), "rve_timing_get")
+        capi.check(capi.lib().rve_timing_get(self.h, kind, C.byref(ms), C.byref(n), C.byref(b)), "rve_timing_get")
         return ms.value, n.value, b.value
 
     def launches(self):
