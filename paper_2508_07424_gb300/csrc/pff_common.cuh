@@ -66,7 +66,7 @@ struct Geom {
 };
 
 // Device scalars of one iterative solve. All solver control that the GPU needs between kernels
-// lives here; the host reads it back only to stop an iteration chunk.
+// lives here; the host reads it back once a solve (one graph launch) has finished.
 struct Scal {
     double rr, rr0, rz, pq, alpha, beta, scale2;
     double abar, bbar, D, Gamma, red[24];

@@ -8,9 +8,12 @@
 //      (Eqs. (SystemDisanyb), (gamFunct), (HistoryNumIni));
 //   3. Anderson mixing of the staggered map phi -> phi(E) (the accelerated staggering of Storvik
 //      et al., cited in Sec. 4.1), stopped by the three ratios of Eq. (errors_crack).
-// Every field operation runs in the kernels of pff_kernels.cuh / pff_functors.cuh; the host
-// keeps only scalar control: the bracketed Illinois search on E, the m x m Anderson
-// least-squares problem and the stopping tests.
+// The monolithic Newton-Raphson increment of Sec. 4.1 (BiCGSTAB on the coupled Jacobian,
+// pff_newton.cuh) is the alternative solver of the same equations (rve_config.solver).
+// Every field operation runs in the kernels of pff_kernels.cuh / pff_functors.cuh /
+// pff_newton.cuh; the host keeps only scalar control: the search on E (secant predictor,
+// bracket, secant/Illinois steps), the m x m Anderson least-squares problem, the BiCGSTAB
+// scalars and the stopping tests.
 #include <cuda_runtime.h>
 #include <sys/stat.h>
 
