@@ -221,7 +221,7 @@ long rve_launch_count(rve_handle h);
  * process-wide table and a cache file of lines "<key> <cw_y> <cw_z>": $PFF_TILE_CACHE, else
  * $XDG_CACHE_HOME/pff_gb300/tiles.txt, else ~/.cache/pff_gb300/tiles.txt (not written if none can
  * be created). PFF_TILE_TUNE=0 keeps the built-in widths, PFF_TILE_CW=<y>,<z> forces admissible
- * ones. Every column is transformed by the same code whatever the width, so results do not
+ * ones (<y> alone for grids without a z pass; inadmissible values are ignored). Every column is transformed by the same code whatever the width, so results do not
  * depend on the choice. Not from the paper: a tuning aid of this implementation. */
 int rve_tile_config(rve_handle h, int *cw_y, int *cw_z);
 

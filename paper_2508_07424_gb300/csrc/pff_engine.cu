@@ -1008,7 +1008,9 @@ struct Engine : EngineBase {
         const char *force = std::getenv("PFF_TILE_CW");
         if (force) {
             int y = 0, z = 0;
-            if (std::sscanf(force, "%d,%d", &y, &z) == 2 && admissible(y, z)) { set_tiles(y, z); return; }
+            const int got = std::sscanf(force, "%d,%d", &y, &z);
+            if (g.nz < 4 && got >= 1) z = cw_z;  // no z pass: only the y width matters
+            if (got >= 1 && admissible(y, z)) { set_tiles(y, z); return; }
         }
         const char *tune = std::getenv("PFF_TILE_TUNE");
         if (tune && std::string(tune) == "0") { set_tiles(cw_y, cw_z); return; }
