@@ -30,6 +30,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pff_rve.h"
 #include "pff_common.cuh"
 #include "pff_functors.cuh"
@@ -56,6 +58,15 @@ struct StatusError {
     } while (0)
 
 thread_local std::string g_last_error;
+
+// NVTX range for profilers (nsys, ncu --nvtx): increments, solves and control evaluations show as
+// named ranges on the host timeline. Without an attached tool the calls return at once.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 // ------------------------------------------------------------------------------------------------
 // Setup kernels
@@ -1227,6 +1238,7 @@ struct Engine : EngineBase {
         return RVE_OK;
     }
     int mech_solve(const T *phi_in, int &iters) {
+        Range nvtx("equilibrium solve");
         if (cfg.split == RVE_SPLIT_SPECTRAL) return mech_solve_split(phi_in, iters);
         return NS == 3 ? mech_solve_t<3>(phi_in, iters) : mech_solve_t<6>(phi_in, iters);
     }
@@ -1392,6 +1404,7 @@ struct Engine : EngineBase {
 
     // phi(E) into phi_trial (warm start = current phi_trial); returns D(phi(E)).
     int damage_eval(double E, double &Dv, int &iters) {
+        Range nvtx("damage solve");
         const int mode = cfg.history ? 0 : 1;
         double Dsol;
         const bool reuse = ddiv_ok;
@@ -1543,6 +1556,7 @@ struct Engine : EngineBase {
 
     // ---- control: smallest E >= 0 with D(phi(E)) = tau (a10) -----------------------------------
     int arc_length(double tau, double E_guess, double &E_out, double &D_out, rve_step_result &st_) {
+        Range nvtx("control search");
         int it = 0, rc;
         ddiv_ok = false;  // phi_trial was just reset to the staggered iterate
         double Ep = -1.0, fp = 0.0;
@@ -1663,6 +1677,7 @@ struct Engine : EngineBase {
     // four levels; each sub-increment is committed as its own point of the load curve.
     bool stag_failed = false, accept_unconverged = false;
     int step(double dtau, rve_step_result *out) override {
+        Range nvtx("increment");
         // the Newton scheme needs E > 0 (psi_o is quadratic in E, so at E = 0 the Jacobian has no
         // coupling from E to the damage): the first increment is taken by the staggered solver
         if (cfg.solver == RVE_SOLVER_NEWTON && S.E > 0.0) return step_newton(dtau, out);
@@ -1820,6 +1835,7 @@ struct Engine : EngineBase {
         return fail(RVE_ENOCONV, "Newton: BiCGSTAB iteration cap");
     }
     int step_newton(double dtau, rve_step_result *out) {
+        Range nvtx("newton increment");
         if (!micro_set) return RVE_ESTATE;
         if (!(dtau > 0.0)) return RVE_EINVAL;
         return NS == 3 ? (D == 2 ? step_newton_t<3, 2>(dtau, out) : step_newton_t<3, 3>(dtau, out))
