@@ -333,6 +333,29 @@ struct PwCommit {
     __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
 };
 
+// Start of the next solve of a control search: with (x_b, d_b) the last solution and its kept
+// divergence and (x_a, d_a) the one before, x_b <- x_b + w (x_b - x_a) (secant extrapolation in E,
+// w = 0: none), likewise d_b, and (x_a, d_a) <- the old (x_b, d_b).
+template <typename T>
+struct PwSecantStart {
+    static constexpr int NR = 0;
+    static constexpr bool MAXRED = false;
+    bool skip_if_done;
+    T *xb, *xa, *db, *da;
+    T w;
+    __device__ void apply(long long v, double *) const {
+        const T pb = xb[v], pa = xa[v], qb = db[v], qa = da[v];
+        xa[v] = pb;
+        da[v] = qb;
+        if (w != (T)0) {
+            xb[v] = pb + w * (pb - pa);
+            db[v] = qb + w * (qb - qa);
+        }
+    }
+    struct Fin { __device__ void operator()(const double *) const {} };
+    __device__ Fin fin(Scal *) const { return Fin{}; }
+};
+
 // Anderson: Gram matrix of the residual differences dF_a = R_{a+1} - R_a (R_j = G_j - X_j) and
 // their products with the newest residual, K <= 5 columns.
 struct AAPtrs {
@@ -1252,6 +1275,12 @@ struct Engine : EngineBase {
     // left it (valid while ddiv_ok): the next solve of the same search starts without transforms
     T *ddiv = nullptr;
     bool ddiv_ok = false;
+    // The evaluation before the last one of the running search (phi, div at E_prev): the next
+    // solve starts from the secant extrapolation in E of the last two solutions. div(K grad phi)
+    // is linear in phi, so the kept divergence extrapolates exactly with it.
+    T *phi_prev = nullptr, *ddiv_prev = nullptr;
+    bool prev_ok = false;
+    double E_last = 0.0, E_prev = 0.0;
     int mech_solve_split(const T *phi_in, int &iters) {
         if (!epsk) epsk = alloc<T>((size_t)3 * N);
         ProSplitStress<T> pst{true, mx, phi_in, lamT, muT, gid, (T)cfg.k_res, {}, N};
@@ -1408,11 +1437,26 @@ struct Engine : EngineBase {
         const int mode = cfg.history ? 0 : 1;
         double Dsol;
         const bool reuse = ddiv_ok;
+        if (reuse) {
+            if (!phi_prev) { phi_prev = alloc<T>(N); ddiv_prev = alloc<T>(N); }
+            double w = 0.0;
+            if (prev_ok && E_last != E_prev) {
+                w = (E - E_last) / (E_last - E_prev);
+                if (!(std::fabs(w) <= 4.0)) w = 0.0;  // far outside the last step: no extrapolation
+            }
+            pointwise(PwSecantStart<T>{false, phi_trial, phi_prev, ddiv, ddiv_prev, (T)w}, sc2);
+            E_prev = E_last;
+            prev_ok = true;
+        } else {
+            prev_ok = false;
+        }
         ddiv_ok = false;
         int rc = pcg(mode, E, dmg_coef(), Hcur, (T)2.0, phi_trial, cfg.tol_dmg, cfg.max_dmg_iters, si.amean,
                      si.bbar, iters, &Dsol, reuse);
-        if (rc) return rc;
+        if (rc) { prev_ok = false; return rc; }
         ddiv_ok = std::isfinite(Dsol);
+        if (ddiv_ok) E_last = E;
+        else prev_ok = false;
         if (std::isfinite(Dsol)) {
             Dv = Dsol;
         } else {
@@ -1559,6 +1603,7 @@ struct Engine : EngineBase {
         Range nvtx("control search");
         int it = 0, rc;
         ddiv_ok = false;  // phi_trial was just reset to the staggered iterate
+        prev_ok = false;
         double Ep = -1.0, fp = 0.0;
         auto evaluate = [&](double E, double &f) -> int {
             double Dv;
@@ -2132,6 +2177,7 @@ struct Engine : EngineBase {
     }
     int damage_eval_api(double E, double &Dv, int &iters) override {
         ddiv_ok = false;
+        prev_ok = false;
         return damage_eval(E, Dv, iters);
     }
     int dissipation_host(const double *phi_host, double &Dv, double &Gv) override {
