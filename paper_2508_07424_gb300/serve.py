@@ -63,18 +63,19 @@ def percentile(xs, q):
     return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
 
 
-def replay(server, requests, time_scale=1.0, **kw):
+def replay(server, requests, time_scale=1.0, clock=time.perf_counter, sleep=time.sleep, **kw):
     """requests: list of (arrival_s, workload, n_inc). Submits each at its (scaled) arrival time,
-    collects every result. Returns (results by id, wall seconds)."""
-    t0 = time.perf_counter()
+    collects every result. Returns (results by id, wall seconds). ``clock`` and ``sleep`` are the
+    time source (replaceable for tests)."""
+    t0 = clock()
     out = {}
     done = threading.Event()
 
     def feeder():
         for i, (ta, w, n_inc) in enumerate(requests):
-            delay = t0 + ta * time_scale - time.perf_counter()
+            delay = t0 + ta * time_scale - clock()
             if delay > 0:
-                time.sleep(delay)
+                sleep(delay)
             rc = server.submit(i, w, n_inc, **kw)
             if rc != capi.RVE_OK:
                 out[i] = {"id": i, "status": rc}
@@ -86,7 +87,7 @@ def replay(server, requests, time_scale=1.0, **kw):
         for r in server.wait(64, 0.5):
             out[r["id"]] = r
     th.join()
-    return out, time.perf_counter() - t0
+    return out, clock() - t0
 
 
 def crack_position_sampling(server, w, positions, n_inc=None, timeout_s=600.0, **kw):
