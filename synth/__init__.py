@@ -482,3 +482,25 @@ def small_cases():
 
 def replace(w, **kw):
     return dataclasses.replace(w, **kw)
+
+
+def config_names():
+    """Names of the seeded workload configurations in configs.json."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "configs.json")) as f:
+        return list(json.load(f))
+
+
+def load_config(name):
+    """Build the workload(s) of a named configuration of configs.json: a generator of this module,
+    its keyword arguments (seeds included) and the precision. Returns a Workload, or a list of
+    them for the batched and serving configurations."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "configs.json")) as f:
+        c = json.load(f)[name]
+    out = globals()[c["generator"]](**c["kwargs"])
+    for w in (out if isinstance(out, list) else [out]):
+        w.precision = c["precision"]
+    return out
