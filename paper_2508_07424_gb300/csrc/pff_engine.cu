@@ -1025,7 +1025,7 @@ struct Engine : EngineBase {
         CK(cudaGetDevice(&dev));
         cudaDeviceProp pr;
         CK(cudaGetDeviceProperties(&pr, dev));
-        char buf[256];
+        char buf[512];
         std::snprintf(buf, sizeof(buf), "%s|sm%d%d|d%d|%dx%dx%d|%s", pr.name, pr.major, pr.minor, D, g.nx, g.ny, g.nz,
                       kSingle ? "fp32" : "fp64");
         std::string k(buf);
