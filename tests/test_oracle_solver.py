@@ -7,7 +7,8 @@ P4  brute force: the unit-load equilibrium equals the minimiser of the elastic e
     displacements assembled with dense DFT derivative matrices (numpy.linalg.lstsq); the damage
     solve equals a dense direct solve of the same operator (numpy.linalg.solve).
 P5  crack-tip enrichment is a fixed point: a damage solve with H = psi_ini returns phi_ini, and
-    psi_ini vanishes away from the two tips (homogeneous Gc, A = I).
+    psi_ini vanishes away from the two tips (homogeneous Gc; A = I and A of Eq. (PFFani) with
+    beta = 2). The anisotropic (Eq. (daminiAni)) and CPFE enrichments equal a dense direct solve.
 P6  1D AT2 profile: with phi pinned to 1 at one voxel the damage solve approaches exp(-|x|/l)
     and Gamma -> 1 as l/h grows (Sec. 2.1, Eqs. (CrackLenght), (CrackLenghtreal)).
 P7  uniform branch of a homogeneous uncracked RVE: phi = sqrt(2 l tau/(Gc V)),
@@ -15,7 +16,11 @@ P7  uniform branch of a homogeneous uncracked RVE: phi = sqrt(2 l tau/(Gc V)),
 P8  without history the model is variational, so the external work V T^n equals the change of
     E_mec + D + int g psi_ini up to the quadrature error of the load curve (Sec. 5.1: the two
     toughness measures coincide without history); the gap vanishes as the increment shrinks.
-R   converged increments make the independently coded residuals R1, R2, R3 vanish.
+R   converged increments make the independently coded residuals R1, R2, R3 vanish (also with the
+    spectral split).
+S   spectral split at system level: stress, drive and energy of a homogeneous cell against
+    Miehe's closed form (tension, compression, mixed signs); the split equilibrium of a damaged
+    laminate against its closed form in tension and in compression.
 """
 import math
 
@@ -353,6 +358,188 @@ def test_converged_increments_zero_residuals():
     model = S.Model(w.micro, S.params_from_workload(w, tol_stag=1e-11))
     st = S.init_state(model)
     for _ in range(3):
+        H_prev = st.H
+        st, _ = S.increment(model, st, w.dtau)
+        r1, r2, r3 = res.check_state(model, st, H_prev)
+        assert r1 < 1e-10 and r2 < 1e-9 and r3 < 1e-11, (r1, r2, r3)
+
+
+# ---- crack-tip enrichment with anisotropic damage, CPFE, and the split at system level -----------
+
+def _dense_helmholtz(model, ell, phi_disc):
+    """Dense direct solve of phi - l^2 div(A grad phi) = phi_disc with explicit DFT derivative
+    matrices: the spectral divergence is -D^T, so the operator is I + l^2 sum_ij D_i^T A_ij D_j."""
+    dim = model.d
+    N = int(np.prod(model.grid))
+    D = [_deriv(model.grid, a) for a in range(dim)]
+    L = np.eye(N)
+    for i in range(dim):
+        for j in range(dim):
+            L += ell * ell * D[i].T @ np.diag(model.A[i, j].reshape(-1)) @ D[j]
+    return np.linalg.solve(L, phi_disc.reshape(-1)).reshape(model.grid), D
+
+
+def _dense_gamma_prime(model, ell, phi, D):
+    """gamma_f'(phi) = Gc/l phi + sum_ij D_i^T (Gc l A_ij) D_j phi (Eq. (gamFunct), dense)."""
+    out = (model.Gc / ell * phi).reshape(-1)
+    for i in range(model.d):
+        for j in range(model.d):
+            out = out + D[i].T @ ((model.Gc * ell * model.A[i, j]).reshape(-1) * (D[j] @ phi.reshape(-1)))
+    return out.reshape(model.grid)
+
+
+def _tip_source(micro):
+    """phi_disc written from the crack's definition (Sec. 4.3): 1 at the first and last voxel of
+    the crack row (every z), 0 elsewhere."""
+    nx, ny, nz = micro.n
+    c = micro.crack
+    src = np.zeros((nz, ny, nx))
+    src[:, c.row, c.x0 % nx] = 1.0
+    src[:, c.row, (c.x0 + c.length - 1) % nx] = 1.0
+    return src
+
+
+@pytest.mark.parametrize("n,dim", [((16, 8), 2), ((8, 4, 4), 3)])
+def test_anisotropic_cte_matches_dense_solve(n, dim):
+    """Eq. (daminiAni) with the cleavage tensor of Eq. (PFFani), beta = 2 (the anisotropic branch
+    of the enrichment solves it by PCG). Against a dense direct solve of the same operator:
+    phi_ini = phi_M phi_o / max phi_o and psi_ini = max(0, gamma'/(2 (1 - phi_ini))) of Eq.
+    (Enini). Catches l A in place of l^2 A, A^T or I in place of A, a wrong tip voxel, a dropped
+    Gc in gamma'."""
+    crack = synth.Crack(synth.CRACK_CTE, row=n[1] // 2, x0=2, length=6, phi_M=0.8)
+    m = synth.voronoi(n, 4, 21, orientation="inplane" if dim == 2 else "so3", beta=2.0, sigma_Gc=0.3,
+                      crack=crack)
+    ell = 1.7
+    model = S.Model(m, S.Params(ell=ell))
+    assert not model.isotropic_damage
+    phi_ini, psi_ini = S.initial_crack(model)
+    phi_o, D = _dense_helmholtz(model, ell, _tip_source(m))
+    ref = 0.8 * phi_o / phi_o.max()
+    np.testing.assert_allclose(phi_ini, ref, rtol=0, atol=1e-12)
+    gp = _dense_gamma_prime(model, ell, ref, D)
+    np.testing.assert_allclose(psi_ini, np.maximum(0.0, gp / (2.0 * (1.0 - ref))), rtol=0,
+                               atol=1e-11 * np.abs(psi_ini).max())
+
+
+@pytest.mark.parametrize("n,dim", [((16, 16), 2), ((8, 8, 4), 3)])
+def test_anisotropic_cte_is_fixed_point_of_damage_solve(n, dim):
+    """With uniform Gc and beta != 0, gamma'(phi_ini) = Gc/l (phi_ini - l^2 div(A grad phi_ini))
+    is a non-negative multiple of the tip source, so H = psi_ini makes phi_ini the solution of the
+    damage equation at E = 0 (Eqs. (Enini), (HistoryNumIni)) exactly, and psi_ini vanishes off
+    the tips."""
+    crack = synth.Crack(synth.CRACK_CTE, row=n[1] // 2, x0=3, length=6, phi_M=0.8)
+    m = synth.voronoi(n, 5, 23, orientation="inplane" if dim == 2 else "so3", beta=2.0, crack=crack)
+    model = S.Model(m, S.Params(ell=2.0, tol_dmg=1e-14))
+    assert not model.isotropic_damage
+    st = S.init_state(model)
+    phi, _ = S.damage_solve(model, st.psi_ini, np.zeros(model.grid))
+    np.testing.assert_allclose(phi, st.phi, rtol=0, atol=1e-11)
+    off = _tip_source(m) == 0.0
+    assert np.abs(st.psi_ini[off]).max() < 1e-10 * st.psi_ini.max()
+
+
+@pytest.mark.parametrize("beta", [0.0, 2.0])
+def test_cpfe_initial_crack_matches_dense_solve(beta):
+    """CPFE (Sec. 4.3): phi_disc = 1 on every voxel of the crack row, so the source is the crack
+    mask itself (written here from the row and the span, not from the oracle's mask). Dense solve
+    of Eq. (damini) / (daminiAni) as above; psi_ini of Eq. (Enini)."""
+    crack = synth.Crack(synth.CRACK_CPFE, row=5, x0=13, length=6, phi_M=0.98)
+    m = synth.voronoi((16, 10), 3, 29, beta=beta, crack=crack)
+    ell = 1.5
+    model = S.Model(m, S.Params(ell=ell))
+    phi_ini, psi_ini = S.initial_crack(model)
+    src = np.zeros(model.grid)
+    for x in range(13, 19):
+        src[0, 5, x % 16] = 1.0
+    assert src.sum() == 6
+    phi_o, D = _dense_helmholtz(model, ell, src)
+    ref = 0.98 * phi_o / phi_o.max()
+    np.testing.assert_allclose(phi_ini, ref, rtol=0, atol=1e-12)
+    gp = _dense_gamma_prime(model, ell, ref, D)
+    np.testing.assert_allclose(psi_ini, np.maximum(0.0, gp / (2.0 * (1.0 - ref))), rtol=0,
+                               atol=1e-11 * np.abs(psi_ini).max())
+
+
+def _miehe_closed_form(e, lam, mu, g):
+    """Miehe's split for a diagonal plane-strain strain diag(a, b) (principal axes x, y, eps_zz = 0):
+    psi+- = lam/2 <a + b>+-^2 + mu (<a>+-^2 + <b>+-^2), sigma = g sigma+ + sigma- with
+    sigma+- = lam <tr>+- I + 2 mu diag(<a>+-, <b>+-)."""
+    a, b = e
+    pos, neg = (lambda v: max(v, 0.0)), (lambda v: min(v, 0.0))
+    tr = a + b
+    pp = 0.5 * lam * pos(tr) ** 2 + mu * (pos(a) ** 2 + pos(b) ** 2)
+    pm = 0.5 * lam * neg(tr) ** 2 + mu * (neg(a) ** 2 + neg(b) ** 2)
+    sp_ = np.diag([lam * pos(tr) + 2 * mu * pos(a), lam * pos(tr) + 2 * mu * pos(b)])
+    sm_ = np.diag([lam * neg(tr) + 2 * mu * neg(a), lam * neg(tr) + 2 * mu * neg(b)])
+    return pp, pm, g * sp_ + sm_
+
+
+@pytest.mark.parametrize("f6", [(0, 1, 0, 0, 0, 0), (0, -1, 0, 0, 0, 0), (-0.5, 1, 0, 0, 0, 0),
+                                (0.3, -1, 0, 0, 0, 0)])
+def test_split_model_energies_and_stress_closed_form(f6):
+    """Model.stress / drive / elastic_energy with the spectral split on a homogeneous RVE at a
+    uniform damage: uniaxial tension, uniaxial compression and two mixed-sign strains against
+    Miehe's closed form. Catches g (sigma+ + sigma-) in place of g sigma+ + sigma-, psi_o in
+    place of psi+ as the drive, and a degraded psi-."""
+    m = synth.homogeneous((8, 8), E=1.3, nu=0.27)
+    model = S.Model(m, S.Params(ell=2.0, split=1, f6=f6))
+    phi = np.full(model.grid, 0.41)
+    g = (1 - 0.41) ** 2 + model.p.k_res
+    _, lam, mu = synth.iso_constants(1.3, 0.27)
+    E = 0.7
+    eps = E * model.fB
+    pp, pm, sig = _miehe_closed_form((E * f6[0], E * f6[1]), lam, mu, g)
+    got = model.stress(eps, phi)
+    np.testing.assert_allclose(got[:, :, 0, 0, 0], sig, rtol=1e-13, atol=1e-15)
+    assert np.ptp(got) < 1e-14 or np.allclose(got, got[:, :, :1, :1, :1], rtol=1e-14, atol=0)
+    np.testing.assert_allclose(model.drive(eps), pp, rtol=1e-13, atol=1e-16)
+    assert abs(model.elastic_energy(eps, phi) - model.V * (g * pp + pm)) <= 1e-13 * model.V * (pp + pm)
+    # the unit-load equilibrium of a homogeneous cell is the uniform strain (no fluctuation)
+    F1, _ = S.mech_solve(model, phi, np.zeros((2, 2) + model.grid))
+    assert np.abs(F1).max() < 1e-14
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_split_laminate_closed_form(sign):
+    """Layers stacked along x with damage constant per layer, load f = sign e_x (x) e_x - 0.25 e_y (x) e_y.
+    Compatibility leaves eps_yy = -0.25 and eps_xy = 0 uniform and eps_xx = a_k per layer with
+    <a_k> = sign; equilibrium makes sigma_xx uniform. Tension (sign = +1, tr > 0 in every layer):
+    g_k (lam_k (a_k - 1/4) + 2 mu_k a_k) = c. Compression (sign = -1, a_k < 0 and tr < 0): the
+    degradation drops out, lam_k (a_k - 1/4) + 2 mu_k a_k = c. So the Newton solve of the split
+    equilibrium has a closed form in both regimes."""
+    widths = [6, 10, 8, 8]
+    phases = [(1.0, 0.3, 1.0), (4.0, 0.2, 1.0), (2.0, 0.35, 1.0), (0.7, 0.25, 1.0)]
+    m = synth.laminate((32, 8), "x", widths, phases)
+    model = S.Model(m, S.Params(ell=2.0, split=1, f6=(sign, -0.25, 0, 0, 0, 0), tol_mech=1e-13))
+    phi_layer = np.repeat([0.1, 0.5, 0.3, 0.7], widths)
+    phi = np.broadcast_to(phi_layer, model.grid).copy()
+    C = np.array([synth.iso_constants(E, nu) for (E, nu, _) in phases])
+    lam = np.repeat(C[:, 1], widths)
+    mu = np.repeat(C[:, 2], widths)
+    g = (1 - phi_layer) ** 2 + model.p.k_res if sign > 0 else np.ones_like(phi_layer)
+    M = lam + 2 * mu
+    # a_k = (c / g_k + lam_k / 4) / M_k with mean(a) = sign
+    c = (sign - np.mean(lam / (4 * M))) / np.mean(1.0 / (g * M))
+    a = (c / g + lam / 4) / M
+    tr = a - 0.25
+    assert (np.all(tr > 0) and np.all(a > 0)) if sign > 0 else (np.all(tr < 0) and np.all(a < 0))
+    F1, it = S.mech_solve(model, phi, np.zeros((2, 2) + model.grid))
+    assert it > 0
+    eps = model.fB + 0.5 * (F1 + np.swapaxes(F1, 0, 1))
+    np.testing.assert_allclose(eps[0, 0][0, 0], a, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(eps[1, 1], -0.25, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(eps[0, 1], 0.0, atol=1e-11)
+    sig = model.stress(eps, phi)
+    np.testing.assert_allclose(sig[0, 0], c, rtol=1e-10)
+
+
+def test_split_converged_increments_zero_residuals():
+    """Increments of the cracked homogeneous cell with the spectral split: the independently coded
+    residuals R1-R3 (with the split stress and psi+ as the history drive) vanish."""
+    w = synth.replace(synth.small_cases()["homog32"], split=1)
+    model = S.Model(w.micro, S.params_from_workload(w, tol_stag=1e-11))
+    st = S.init_state(model)
+    for _ in range(2):
         H_prev = st.H
         st, _ = S.increment(model, st, w.dtau)
         r1, r2, r3 = res.check_state(model, st, H_prev)
