@@ -149,6 +149,11 @@ typedef struct {
 
 void rve_config_default(rve_config *cfg);
 
+/* Check a configuration without allocating anything: the checks rve_create makes before it
+ * allocates (listed there). Returns RVE_OK or RVE_EINVAL (rve_strerror / the last-error message
+ * says why for the grid-size rule). rve_server_submit runs it before it copies a request. */
+int rve_config_validate(const rve_config *cfg);
+
 /* Allocate the device state of one RVE. cfg is copied. Errors: RVE_EINVAL (grid not a power of
  * two in [4, 1024], dim/nz mismatch, grid too small for one warp per x-pass CTA, i.e.
  * (nx/4) * min(128/(nx/4), ny*nz/2) < 32, ell <= 0, unsupported precision), RVE_ENOMEM, RVE_ECUDA. */
@@ -268,20 +273,31 @@ int rve_server_destroy(rve_server s);
  * latency-critical loop that must not hit the implicit synchronisation of cudaMalloc/cudaFree,
  * an embedded caller with a fixed memory budget). The paper has no counterpart: it is a service
  * entry point of this library, computing the same values as rve_dissipation.
- *   All pointers are DEVICE pointers owned by the caller: grain_id [n_vox] (x fastest),
+ *   All pointers are DEVICE pointers owned by the caller: grain_id [n_vox] (x fastest), each
+ *   id in [0, n_grains) (an id outside that range reads no table entry and makes out NaN),
  *   Gc [n_grains], A [n_grains][6] (cleavage tensor of Eq. (PFFani); 3D order xx, yy, zz, yz,
  *   xz, xy; 2D uses slots 0, 1, 2 for xx, yy, xy), phi [n_vox]; out [2] receives D and Gamma.
  *   stream: cudaStream_t or NULL. The call is asynchronous on that stream.
  * Scratch: one fixed 8 MiB __device__ array inside the library, held by every GPU that loads it
  * until the process exits; nothing is allocated. Grids whose spectra and partial sums do not fit
- * (e.g. 2D above 512 x 512, 3D above 32^3) return RVE_EINVAL with a message on stderr; so do
- * grids too small for one warp per x-pass CTA (as for rve_create).
+ * (e.g. 2D grids of more than 512 x 512 voxels such as 1024 x 512, 3D above 32^3) return RVE_EINVAL with a message on
+ * stderr; so do grids too small for one warp per x-pass CTA (as for rve_create). Extents are
+ * powers of two from 4 to 1024; dim = 3 also takes plates one voxel thick (n[2] = 1), as
+ * rve_create does.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress), so
  * make that first call before any stream capture. All calls share the array: calls that
  * overlap on the GPU (different streams, different host threads) race and must be ordered by
  * the caller. Each call clears the parts of the array it relies on. */
 int rve_dissipation_noalloc(int dim, const int n[3], double ell, int n_grains, const int32_t *grain_id,
                             const double *Gc, const double *A, const double *phi, double *out, void *stream);
+
+/* Measured FP64 fused multiply-add rate of the current device, for the roofline of the FP64
+ * path (the paper has no counterpart: a measurement helper of this library). Launches one
+ * warm-up and one timed kernel of 8 blocks per SM x 256 threads, each thread running 8
+ * independent chains of iters x 16 FMAs, timed with CUDA events on `stream` (cudaStream_t or
+ * NULL); blocks until done. tflops receives 2 x FMAs / time in TFLOP/s, ms_out (optional) the
+ * kernel time. Errors: RVE_EINVAL (iters < 1, tflops NULL), RVE_ECUDA. */
+int rve_fp64_fma_rate(int iters, double *tflops, double *ms_out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -59,6 +59,8 @@ _dp = C.POINTER(C.c_double)
 
 _SIGS = {
     "rve_config_default": (None, [C.POINTER(rve_config)]),
+    "rve_config_validate": (C.c_int, [C.POINTER(rve_config)]),
+    "rve_fp64_fma_rate": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),
     "rve_create": (C.c_int, [C.POINTER(rve_config), C.POINTER(rve_handle)]),
     "set_microstructure": (C.c_int, [rve_handle, C.POINTER(rve_micro)]),
     "step_dissipation": (C.c_int, [rve_handle, C.c_double, C.POINTER(rve_step_result)]),

@@ -2342,9 +2342,8 @@ void rve_config_default(rve_config *c) {
 
 static bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
 
-int rve_create(const rve_config *cfg, rve_handle *out) {
-    if (!cfg || !out) return RVE_EINVAL;
-    *out = nullptr;
+int rve_config_validate(const rve_config *cfg) {
+    if (!cfg) return RVE_EINVAL;
     if (cfg->dim != 2 && cfg->dim != 3) return RVE_EINVAL;
     if (!pow2_in(cfg->n[0], 4, 1024) || !pow2_in(cfg->n[1], 4, 1024)) return RVE_EINVAL;
     if (cfg->dim == 2 && cfg->n[2] != 1) return RVE_EINVAL;
@@ -2371,6 +2370,13 @@ int rve_create(const rve_config *cfg, rve_handle *out) {
         return RVE_EINVAL;
     }
     if (cfg->precision != RVE_FP64 && cfg->precision != RVE_FP32R) return RVE_EINVAL;
+    return RVE_OK;
+}
+
+int rve_create(const rve_config *cfg, rve_handle *out) {
+    if (!cfg || !out) return RVE_EINVAL;
+    *out = nullptr;
+    if (int rc = rve_config_validate(cfg)) return rc;
     GUARD_BEGIN
     auto *h = new rve_s();
     h->cfg = *cfg;

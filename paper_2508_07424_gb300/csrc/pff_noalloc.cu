@@ -71,6 +71,48 @@ __global__ void k_twiddles(double2 *tw, int L) {
     tw[m] = make_double2(c, s);
 }
 
+// Epilogue of the last pass: the dissipation density of Eq. (CrackLenght_ani) summed with and
+// without Gc, as the engine's, but with the grain ids checked against n_grains before they index
+// the caller's tables. The ids come from caller memory that this entry point cannot validate on
+// the host, so an id outside [0, n_grains) reads no table entry and turns both sums into NaN.
+template <int D>
+struct EpiDissChecked {
+    static constexpr int NR = 2;
+    bool skip_if_done;
+    const double *phi;
+    const double *GcTab, *Atab;
+    const int *gid;
+    int n_grains;
+    double ell;
+    __device__ void apply(long long v, const double *gr, double *acc) const {
+        const int gg = gid[v];
+        if (gg < 0 || gg >= n_grains) {
+            const double nan = __longlong_as_double(0x7ff8000000000000LL);
+            acc[0] += nan;
+            acc[1] += nan;
+            return;
+        }
+        const double *A = Atab + (size_t)gg * 6;
+        double q;
+        if constexpr (D == 2) {
+            q = gr[0] * (A[0] * gr[0] + A[2] * gr[1]) + gr[1] * (A[2] * gr[0] + A[1] * gr[1]);
+        } else {
+            q = gr[0] * (A[0] * gr[0] + A[5] * gr[1] + A[4] * gr[2]) +
+                gr[1] * (A[5] * gr[0] + A[1] * gr[1] + A[3] * gr[2]) +
+                gr[2] * (A[4] * gr[0] + A[3] * gr[1] + A[2] * gr[2]);
+        }
+        const double p = phi[v];
+        const double dens = p * p / (2.0 * ell) + 0.5 * ell * q;
+        acc[0] += GcTab[gg] * dens;
+        acc[1] += dens;
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const { sc->D = t[0]; sc->Gamma = t[1]; }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
 }  // namespace pffnoalloc
 
 using namespace pffnoalloc;
@@ -82,7 +124,8 @@ extern "C" int rve_dissipation_noalloc(int dim, const int n[3], double ell, int 
     if (dim != 2 && dim != 3) return RVE_EINVAL;
     auto pow2 = [](int v) { return v >= 4 && v <= 1024 && (v & (v - 1)) == 0; };
     const int nx = n[0], ny = n[1], nz = dim == 2 ? 1 : n[2];
-    if (!pow2(nx) || !pow2(ny) || (dim == 2 ? n[2] != 1 : !pow2(nz))) return RVE_EINVAL;
+    // 3D plates one voxel thick (nz = 1) are accepted as by rve_create: no z transform
+    if (!pow2(nx) || !pow2(ny) || (dim == 2 ? n[2] != 1 : (nz != 1 && !pow2(nz)))) return RVE_EINVAL;
 
     Geom g{};
     g.d = dim; g.ns = dim == 2 ? 3 : 6;
@@ -173,21 +216,31 @@ extern "C" int rve_dissipation_noalloc(int dim, const int n[3], double ell, int 
     if (dim == 2) {
         if (axis_launch(k_axis<double, 1, 2, AX_FWD_OP_INV, OpGrad<double2, 2>>, 1, 2, OpGrad<double2, 2>{false, xi}, twy))
             return RVE_ECUDA;
-        auto k = k_x_inv<double, 2, EpiDiss<double, 2>>;
+        auto k = k_x_inv<double, 2, EpiDissChecked<2>>;
         const size_t sm = smx * 2;
         if (sm > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k<<<xblocks, xthreads, sm, st>>>(g, spec, EpiDiss<double, 2>{false, phi, Gc, A, gid, ell}, twx, partials, sc);
+        k<<<xblocks, xthreads, sm, st>>>(g, spec, EpiDissChecked<2>{false, phi, Gc, A, gid, n_grains, ell}, twx,
+                                         partials, sc);
     } else {
-        if (axis_launch(k_axis<double, 1, 1, AX_FWD, OpGrad<double2, 3>>, 1, 1, OpGrad<double2, 3>{false, xi}, twy))
-            return RVE_ECUDA;
-        if (axis_launch(k_axis<double, 1, 3, AX_FWD_OP_INV, OpGrad<double2, 3>>, 2, 3, OpGrad<double2, 3>{false, xi}, twz))
-            return RVE_ECUDA;
-        if (axis_launch(k_axis<double, 3, 3, AX_INV, OpGrad<double2, 3>>, 1, 3, OpGrad<double2, 3>{false, xi}, twy))
-            return RVE_ECUDA;
-        auto k = k_x_inv<double, 3, EpiDiss<double, 3>>;
+        if (nz == 1) {
+            // plate: xi_z = 0, so the gradient is taken in the y pass, as in 2D
+            if (axis_launch(k_axis<double, 1, 3, AX_FWD_OP_INV, OpGrad<double2, 3>>, 1, 3, OpGrad<double2, 3>{false, xi},
+                            twy))
+                return RVE_ECUDA;
+        } else {
+            if (axis_launch(k_axis<double, 1, 1, AX_FWD, OpGrad<double2, 3>>, 1, 1, OpGrad<double2, 3>{false, xi}, twy))
+                return RVE_ECUDA;
+            if (axis_launch(k_axis<double, 1, 3, AX_FWD_OP_INV, OpGrad<double2, 3>>, 2, 3, OpGrad<double2, 3>{false, xi},
+                            twz))
+                return RVE_ECUDA;
+            if (axis_launch(k_axis<double, 3, 3, AX_INV, OpGrad<double2, 3>>, 1, 3, OpGrad<double2, 3>{false, xi}, twy))
+                return RVE_ECUDA;
+        }
+        auto k = k_x_inv<double, 3, EpiDissChecked<3>>;
         const size_t sm = smx * 3;
         if (sm > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k<<<xblocks, xthreads, sm, st>>>(g, spec, EpiDiss<double, 3>{false, phi, Gc, A, gid, ell}, twx, partials, sc);
+        k<<<xblocks, xthreads, sm, st>>>(g, spec, EpiDissChecked<3>{false, phi, Gc, A, gid, n_grains, ell}, twx,
+                                         partials, sc);
     }
     if (cudaGetLastError() != cudaSuccess) return RVE_ECUDA;
     // D and Gamma were written to the scalar block by the last CTA; hand them to the caller.

@@ -165,6 +165,9 @@ int rve_server_create(int max_inflight, size_t hbm_budget_bytes, rve_server *out
 int rve_server_submit(rve_server sv, long id, const rve_config *cfg, const rve_micro *m, int n_inc, double dtau) {
     if (!sv || !cfg || !m || !m->grain_id || !m->C_cubic || !m->R || !m->Gc || n_inc < 1 || !(dtau > 0))
         return RVE_EINVAL;
+    // the grid fixes how many grain ids are copied below: check it (as rve_create will) first
+    if (int rc = rve_config_validate(cfg)) return rc;
+    if (m->n_grains <= 0) return RVE_EINVAL;
     auto q = std::make_unique<Request>();
     q->id = id;
     q->cfg = *cfg;
@@ -174,7 +177,6 @@ int rve_server_submit(rve_server sv, long id, const rve_config *cfg, const rve_m
     q->bytes = rve_footprint_bytes(cfg);
     const size_t N = (size_t)cfg->n[0] * cfg->n[1] * (cfg->dim == 3 ? cfg->n[2] : 1);
     const int G = m->n_grains;
-    if (G <= 0) return RVE_EINVAL;
     q->gid.assign(m->grain_id, m->grain_id + N);
     q->Cc.assign(m->C_cubic, m->C_cubic + 3 * G);
     q->R.assign(m->R, m->R + 9 * G);

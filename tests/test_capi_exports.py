@@ -50,6 +50,9 @@ def test_create_rejects_bad_sizes_without_touching_the_gpu(lib):
         cfg = make_config(b["dim"], b["n"], 2.0)
         h = capi.rve_handle()
         assert lib.rve_create(C.byref(cfg), C.byref(h)) == capi.RVE_EINVAL, b
+        assert lib.rve_config_validate(C.byref(cfg)) == capi.RVE_EINVAL, b
+    for n, dim in (((64, 64, 1), 2), ((32, 32, 32), 3), ((256, 128, 1), 3)):
+        assert lib.rve_config_validate(C.byref(make_config(dim, n, 2.0))) == capi.RVE_OK, n
     # the Newton solver: FP64 only, no split
     for kw in (dict(precision=capi.RVE_FP32R), dict(split=capi.RVE_SPLIT_SPECTRAL), dict(solver_bad=True)):
         cfg = make_config(2, (64, 64, 1), 2.0, solver=capi.RVE_SOLVER_NEWTON,
