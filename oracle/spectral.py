@@ -29,11 +29,29 @@ def xi_tilde(shape):
     return out
 
 
+# FFT backend: None runs numpy.fft (one thread); an integer n runs scipy.fft with n worker threads.
+# Both compute the same DFT; the switch exists so that the CPU baseline can also be timed on all
+# host cores. Every test runs with the default.
+_WORKERS = None
+
+
+def set_fft_workers(n):
+    """Select the FFT backend (None: numpy.fft, single-threaded; n >= 1: scipy.fft, n threads)."""
+    global _WORKERS
+    _WORKERS = None if n is None else int(n)
+
+
 def fft(u):
+    if _WORKERS:
+        import scipy.fft
+        return scipy.fft.fftn(u, axes=(-3, -2, -1), workers=_WORKERS)
     return np.fft.fftn(u, axes=(-3, -2, -1))
 
 
 def ifft_real(U):
+    if _WORKERS:
+        import scipy.fft
+        return scipy.fft.ifftn(U, axes=(-3, -2, -1), workers=_WORKERS).real
     return np.fft.ifftn(U, axes=(-3, -2, -1)).real
 
 

@@ -76,3 +76,17 @@ def test_galerkin_annihilates_airy_stress():
     sig[1, 1] = d2(0, 0)
     sig[0, 1] = sig[1, 0] = -d2(0, 1)
     assert np.abs(sp.galerkin_G(sig, 2)).max() < 1e-12 * np.abs(sig).max()
+
+
+def test_threaded_fft_backend_gives_the_same_transform():
+    """The scipy.fft backend (used only to time the CPU baseline on all host cores) computes the
+    same DFT as numpy.fft, to rounding."""
+    rng = np.random.default_rng(9)
+    u = rng.standard_normal((4, 8, 16))
+    ref_f, ref_g = sp.fft(u), sp.grad(u, 3)
+    try:
+        sp.set_fft_workers(2)
+        f, g = sp.fft(u), sp.grad(u, 3)
+    finally:
+        sp.set_fft_workers(None)
+    assert np.abs(f - ref_f).max() < 1e-12 and np.abs(g - ref_g).max() < 1e-12
