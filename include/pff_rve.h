@@ -175,6 +175,33 @@ int set_microstructure(rve_handle h, const rve_micro *m);
  * it was before the call. */
 int step_dissipation(rve_handle h, double dtau, rve_step_result *out);
 
+/* One dissipation increment of each of n handles (1 <= n <= 256, distinct), in lockstep: a host
+ * thread per handle runs that handle's own control (staggered loop, control search, Anderson
+ * mixing) exactly as step_dissipation does, while the iteration loops of the equilibrium and
+ * damage solves of all handles are launched together, one kernel launch per pass serving every
+ * handle (at most 16 per launch), until each handle's own solve has converged. Each handle's
+ * results are bit-identical to stepping it alone with step_dissipation. dtau[i] > 0 per handle;
+ * out (NULL or n records) receives the step results. The handles must share the grid, the
+ * precision and the column tiles, use the staggered solver without the energy split and have
+ * timing off (else RVE_EINVAL, nothing stepped). Returns RVE_OK when every increment succeeded,
+ * else the status of the lowest-index handle that failed; the other handles' increments are
+ * committed all the same. Blocks until all increments are done. Not from the paper: the batching
+ * pattern of this library (many RVEs per launch). */
+int rve_step_batch(rve_handle *hs, int n, const double *dtau, rve_step_result *out);
+
+/* A lockstep group for callers that step handles from threads of their own (the request server):
+ * each rve_step_in_group call runs one increment of h like step_dissipation, and while it runs,
+ * its solve loops are launched together with those of the other handles of the group that are
+ * stepping at the same time (opportunistic batching; results stay bit-identical to stepping
+ * alone). Handles of one group must share grid, precision and column tiles and use the staggered
+ * solver without the split (RVE_EINVAL otherwise, checked per call for the handle's own
+ * configuration). The group owns a coordinator thread and a stream; destroy it only when no
+ * rve_step_in_group call on it is running. */
+typedef struct rve_batch_group_s *rve_batch_group;
+int rve_batch_group_create(rve_batch_group *out);
+int rve_step_in_group(rve_handle h, rve_batch_group g, double dtau, rve_step_result *out);
+int rve_batch_group_destroy(rve_batch_group g);
+
 /* Effective toughness of Eqs. (JaviGc)/(ABC): G = V / A_g (T^F - 1/2 Sigma^F E^F), V = voxel
  * count, A_g = (nx - crack_len) (x nz in 3D). RVE_ENOTFRACTURED until the fracture point. */
 int effective_toughness(rve_handle h, double *g_eff);
@@ -208,14 +235,22 @@ int rve_dissipation(rve_handle h, const double *phi_host, double *D, double *Gam
 int rve_save(rve_handle h, void *buf, size_t *len);
 int rve_load(rve_handle h, const void *buf, size_t len);
 
-/* Per-kernel device timing (CUDA events around every launch of the named kernel class while
- * enabled). kind: 0 = the mechanics projection pass (y/z FFT + projection + inverse); 1 = every
- * column pass (k_axis: the mechanics projection and the damage gradient, divergence and
- * preconditioner passes). bytes_per_launch is the average of the half-spectrum components read
- * and written per launch. While timing is on, solves launch one iteration at a time (no graphs,
- * no launch past convergence). */
+/* Per-kernel device timing (CUDA events around every launch while enabled; rve_timing_enable
+ * with on = 1 also clears what was recorded). kind selects the launches summed:
+ *   0 = the mechanics projection pass (y/z FFT + projection + inverse),
+ *   1 = every column pass (k_axis: projection, damage gradient / divergence / preconditioner),
+ *   2 = k_x_fwd, 3 = k_x_inv, 4 = k_x_mid (the x-axis passes with their fused pointwise work),
+ *   5 = k_pointwise, 6 = all of the above.
+ * total_ms: summed event time; launches: count; bytes_per_launch: average algorithmic bytes
+ * (half-spectrum components read and written over the nx/2 + 1 columns, plus the field words
+ * the fused prologue / epilogue reads and writes per voxel); flops_per_launch: average FFT flops
+ * (5 L log2 L per transformed line of L points, none for pointwise kernels). While timing is on,
+ * solves launch one iteration at a time (no graphs, no launch past convergence). RVE_EINVAL for
+ * an unknown kind. Not from the paper: measurement support of this implementation. */
 int rve_timing_enable(rve_handle h, int on);
 int rve_timing_get(rve_handle h, int kind, double *total_ms, long *launches, double *bytes_per_launch);
+int rve_timing_get_flops(rve_handle h, int kind, double *total_ms, long *launches, double *bytes_per_launch,
+                         double *flops_per_launch);
 
 /* Number of kernels this handle launched so far. */
 long rve_launch_count(rve_handle h);
@@ -265,6 +300,10 @@ int rve_server_submit(rve_server s, long id, const rve_config *cfg, const rve_mi
 /* Collect up to max finished results; waits up to timeout_s seconds for at least one (0: poll). */
 int rve_server_wait(rve_server s, rve_request_result *out, int max, double timeout_s, int *n_out);
 int rve_server_stats(rve_server s, int *peak_inflight, size_t *peak_bytes, long *pending);
+/* Lockstep batching of the requests of one size class (grid, precision; staggered solver without
+ * the split) through a shared rve_batch_group: on (the default) or off (every request steps on its
+ * own). Results are the same either way. Set it before submitting. */
+int rve_server_set_batching(rve_server s, int on);
 /* Finishes every submitted request, then joins the workers. */
 int rve_server_destroy(rve_server s);
 
@@ -284,7 +323,8 @@ int rve_server_destroy(rve_server s);
  * stderr; so do grids too small for one warp per x-pass CTA (as for rve_create). Extents are
  * powers of two from 4 to 1024; dim = 3 also takes plates one voxel thick (n[2] = 1), as
  * rve_create does.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress), so
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
+ * copies a small table of FFT twiddles into the library's constant memory, so
  * make that first call before any stream capture. All calls share the array: calls that
  * overlap on the GPU (different streams, different host threads) race and must be ordered by
  * the caller. Each call clears the parts of the array it relies on. */

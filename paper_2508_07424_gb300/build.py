@@ -6,7 +6,8 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libpff_gb300.so")
-SOURCES = [os.path.join(HERE, "csrc", f) for f in ("pff_engine.cu", "pff_noalloc.cu", "pff_serve.cu", "pff_peak.cu")]
+SOURCES = [os.path.join(HERE, "csrc", f) for f in ("pff_engine_f64.cu", "pff_engine_f32.cu", "pff_capi.cu", "pff_noalloc.cu", "pff_serve.cu",
+                                                       "pff_peak.cu")]
 # every header of csrc/ and include/: an edit to any of them rebuilds the library
 HEADERS = sorted(os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc")) if f.endswith(".cuh")) + [
     os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include"))) if f.endswith(".h")]

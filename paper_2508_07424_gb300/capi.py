@@ -64,6 +64,10 @@ _SIGS = {
     "rve_create": (C.c_int, [C.POINTER(rve_config), C.POINTER(rve_handle)]),
     "set_microstructure": (C.c_int, [rve_handle, C.POINTER(rve_micro)]),
     "step_dissipation": (C.c_int, [rve_handle, C.c_double, C.POINTER(rve_step_result)]),
+    "rve_step_batch": (C.c_int, [C.POINTER(rve_handle), C.c_int, C.POINTER(C.c_double), C.POINTER(rve_step_result)]),
+    "rve_batch_group_create": (C.c_int, [C.POINTER(C.c_void_p)]),
+    "rve_step_in_group": (C.c_int, [rve_handle, C.c_void_p, C.c_double, C.POINTER(rve_step_result)]),
+    "rve_batch_group_destroy": (C.c_int, [C.c_void_p]),
     "effective_toughness": (C.c_int, [rve_handle, _dp]),
     "effective_toughness_functional": (C.c_int, [rve_handle, _dp]),
     "rve_get_field": (C.c_int, [rve_handle, C.c_int, _dp, C.c_size_t]),
@@ -77,6 +81,8 @@ _SIGS = {
     "rve_load": (C.c_int, [rve_handle, C.c_void_p, C.c_size_t]),
     "rve_timing_enable": (C.c_int, [rve_handle, C.c_int]),
     "rve_timing_get": (C.c_int, [rve_handle, C.c_int, _dp, C.POINTER(C.c_long), _dp]),
+    "rve_timing_get_flops": (C.c_int, [rve_handle, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_long),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "rve_launch_count": (C.c_long, [rve_handle]),
     "rve_tile_config": (C.c_int, [rve_handle, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "rve_destroy": (C.c_int, [rve_handle]),
@@ -89,6 +95,7 @@ _SIGS = {
                                   C.POINTER(C.c_int)]),
     "rve_server_stats": (C.c_int, [rve_server, C.POINTER(C.c_int), C.POINTER(C.c_size_t), C.POINTER(C.c_long)]),
     "rve_server_destroy": (C.c_int, [rve_server]),
+    "rve_server_set_batching": (C.c_int, [rve_server, C.c_int]),
     "rve_dissipation_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_double, C.c_int, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }

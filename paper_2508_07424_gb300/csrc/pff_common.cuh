@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 namespace pff {
@@ -16,6 +17,9 @@ namespace pff {
 template <typename T> struct cplx_of;
 template <> struct cplx_of<double> { typedef double2 type; };
 template <> struct cplx_of<float> { typedef float2 type; };
+template <typename C> struct real_of;
+template <> struct real_of<double2> { typedef double type; };
+template <> struct real_of<float2> { typedef float type; };
 
 // Load of a field that no thread of the running kernel writes before reading it (each voxel is
 // read, then possibly rewritten, by the one thread that owns it). The read-only path lets the
@@ -72,6 +76,7 @@ struct Scal {
     double abar, bbar, D, Gamma, red[24];
     int done, iters, flag, first, max_iters, pad_;
     double tol2;
+    double eta2;  // inner stop of a refinement pass: <r, r> <= eta2 <r0, r0> (0: none)
     unsigned int counter;
 };
 

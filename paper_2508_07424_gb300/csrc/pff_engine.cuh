@@ -14,6 +14,8 @@
 // pff_newton.cuh; the host keeps only scalar control: the search on E (secant predictor,
 // bracket, secant/Illinois steps), the m x m Anderson least-squares problem, the BiCGSTAB
 // scalars and the stopping tests.
+#pragma once
+
 #include <cuda_runtime.h>
 #include <sys/stat.h>
 
@@ -28,11 +30,13 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/pff_rve.h"
+#include "pff_batch.cuh"
 #include "pff_common.cuh"
 #include "pff_functors.cuh"
 #include "pff_kernels.cuh"
@@ -57,7 +61,7 @@ struct StatusError {
         if (e_ != cudaSuccess) throw CudaError{e_, #call};               \
     } while (0)
 
-thread_local std::string g_last_error;
+inline thread_local std::string g_last_error;
 
 // NVTX range for profilers (nsys, ncu --nvtx): increments, solves and control evaluations show as
 // named ranges on the host timeline. Without an attached tool the calls return at once.
@@ -131,7 +135,7 @@ __global__ void k_build_tables(int G, int dim, const double *Cc, const double *R
     mu[gg] = (T)(mult * c44);
 }
 
-__global__ void k_crack_setup(long long N, int nx, int ny, const int *gid0, int G, int kind, int row, int x0,
+static __global__ void k_crack_setup(long long N, int nx, int ny, const int *gid0, int G, int kind, int row, int x0,
                               int len, int *gid, double *phi_disc) {
     long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (v >= N) return;
@@ -154,14 +158,55 @@ __global__ void k_crack_setup(long long N, int nx, int ny, const int *gid0, int 
 // Loop condition of a solve captured as a conditional (while) graph node: keep iterating while
 // the device scalars say the solve is not done. The solve always ends: the update kernels set
 // done at convergence, at the iteration cap, on breakdown and on a non-finite scalar.
-__global__ void k_loop_cond(cudaGraphConditionalHandle h, const Scal *sc) {
+static __global__ void k_loop_cond(cudaGraphConditionalHandle h, const Scal *sc) {
     cudaGraphSetConditional(h, sc->done ? 0u : 1u);
 }
 
-__global__ void k_init_scal(Scal *sc, double tol2, int max_iters, double abar, double bbar) {
+static __global__ void k_init_scal(Scal *sc, double tol2, int max_iters, double abar, double bbar, double eta2) {
     sc->done = 0; sc->flag = 0; sc->iters = 0; sc->first = 1; sc->max_iters = max_iters;
     sc->tol2 = tol2; sc->beta = 0.0; sc->alpha = 0.0; sc->counter = 0u; sc->abar = abar; sc->bbar = bbar;
+    sc->eta2 = eta2;
 }
+
+// The correction d of one refinement pass, projected onto compatible strains and added to the
+// FP64 solution: x += P[d], d = 0. The FP32 CG leaves rounding-level parts in d that are not
+// compatible; those whose stress is divergence-free are invisible to the equilibrium residual
+// P[g C : (f + x)], so without the projection they would accumulate in x (and in the stress)
+// while the FP64 residual converges. P (the symmetric-strain Galerkin projection) is the
+// orthogonal projection onto compatible, mean-free strain fields.
+template <typename T, int NS>
+struct ProCorrection {  // d, the field to project
+    static constexpr int NR = 0;
+    static constexpr int RW = NS;
+    bool skip_if_done;
+    const T *d;
+    long long N;
+    __device__ void eval(long long v, T *out, double *) const {
+#pragma unroll
+        for (int a = 0; a < NS; ++a) out[a] = ldro(d + a * N + v);
+    }
+    struct Fin { __device__ void operator()(const double *) const {} };
+    __device__ Fin fin(Scal *) const { return Fin{}; }
+};
+template <typename T, int NS>
+struct EpiAddCorrection {  // x += P[d] (FP64), d = 0
+    static constexpr int NR = 0;
+    static constexpr int RW = 3 * NS;  // x read + written (double), d written
+    bool skip_if_done;
+    double *x;
+    T *d;
+    long long N;
+    __device__ void apply(long long v, const T *val, double *) const {
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+            const size_t i = (size_t)a * N + v;
+            x[i] += (double)val[a];
+            d[i] = (T)0;
+        }
+    }
+    struct Fin { __device__ void operator()(const double *) const {} };
+    __device__ Fin fin(Scal *) const { return Fin{}; }
+};
 
 // ---- pointwise functors used by the engine ------------------------------------------------------
 template <typename T>
@@ -501,7 +546,7 @@ struct PwEpsK {
 };
 
 // Inner (Newton) CG stopping test relative to the initial residual.
-__global__ void k_inner_tol(Scal *sc, double eta2) {
+static __global__ void k_inner_tol(Scal *sc, double eta2) {
     if (!sc->done) { sc->tol2 = eta2; sc->scale2 = sc->rr0; }
 }
 
@@ -580,7 +625,7 @@ template <typename C> struct OpNone {
 // ------------------------------------------------------------------------------------------------
 // Small dense helper: pseudo-inverse solve of a symmetric PSD m x m system by cyclic Jacobi.
 // ------------------------------------------------------------------------------------------------
-static void pinv_solve(int m, const double *Min, const double *b, double rcond, double *x) {
+inline void pinv_solve(int m, const double *Min, const double *b, double rcond, double *x) {
     double A[5][5], V[5][5];
     for (int i = 0; i < m; ++i)
         for (int j = 0; j < m; ++j) { A[i][j] = Min[i * m + j]; V[i][j] = (i == j); }
@@ -629,12 +674,12 @@ static void pinv_solve(int m, const double *Min, const double *b, double rcond, 
 // Column-tile table of the autotuner: process-wide, backed by a text cache file of lines
 // "<key> <cw_y> <cw_z>" (the last line for a key wins).
 // ------------------------------------------------------------------------------------------------
-static std::mutex g_tile_mu;
-static std::mutex g_tune_mu;  // one measurement at a time, so concurrent handles do not skew it
-static std::map<std::string, std::pair<int, int>> g_tiles;
-static bool g_tiles_loaded = false;
+inline std::mutex g_tile_mu;
+inline std::mutex g_tune_mu;  // one measurement at a time, so concurrent handles do not skew it
+inline std::map<std::string, std::pair<int, int>> g_tiles;
+inline bool g_tiles_loaded = false;
 
-static std::string tile_cache_path() {
+inline std::string tile_cache_path() {
     const char *p = std::getenv("PFF_TILE_CACHE");
     if (p && *p) return p;
     const char *x = std::getenv("XDG_CACHE_HOME");
@@ -648,7 +693,7 @@ static std::string tile_cache_path() {
     return base + "/pff_gb300/tiles.txt";
 }
 
-static void tile_load_locked() {
+inline void tile_load_locked() {
     if (g_tiles_loaded) return;
     g_tiles_loaded = true;
     const std::string path = tile_cache_path();
@@ -661,7 +706,7 @@ static void tile_load_locked() {
     std::fclose(f);
 }
 
-static bool tile_lookup(const std::string &key, int &y, int &z) {
+inline bool tile_lookup(const std::string &key, int &y, int &z) {
     std::lock_guard<std::mutex> lk(g_tile_mu);
     tile_load_locked();
     auto it = g_tiles.find(key);
@@ -671,7 +716,7 @@ static bool tile_lookup(const std::string &key, int &y, int &z) {
     return true;
 }
 
-static void tile_store(const std::string &key, int y, int z) {
+inline void tile_store(const std::string &key, int y, int z) {
     std::lock_guard<std::mutex> lk(g_tile_mu);
     tile_load_locked();
     g_tiles[key] = {y, z};
@@ -698,6 +743,7 @@ struct EngineBase {
     rve_config cfg;
     Geom g;
     int cw_y = 2, cw_z = 2;  // column tile widths of the y and z passes (autotuned)
+    int aw = 16;             // warps per CTA of the column passes at most (PFF_AXIS_WARPS)
     cudaStream_t st = nullptr;
     bool own_stream = false;
     int NS = 3, D = 2;
@@ -708,6 +754,7 @@ struct EngineBase {
     long launches = 0;
     int crack_len_ = 0;
     bool timing = false;
+    Batcher *batcher = nullptr;  // set while the handle steps inside rve_step_batch (lockstep solves)
     virtual ~EngineBase() {}
     virtual int set_micro(const rve_micro *m) = 0;
     virtual int step(double dtau, rve_step_result *out) = 0;
@@ -720,7 +767,7 @@ struct EngineBase {
     virtual void save_state(char *p) = 0;
     virtual void load_state(const char *p) = 0;
     virtual void timing_reset() = 0;
-    virtual void timing_get(int kind, double &ms, long &n, double &bytes) = 0;
+    virtual void timing_get(int kind, double &ms, long &n, double &bytes, double &flops) = 0;
     double crack_area() const { return (double)(g.nx - crack_len_) * (D == 3 ? g.nz : 1); }
     double toughness_value() const { return (double)N / crack_area() * (S.T - 0.5 * S.Sigma * S.E); }
     double toughness_functional_value() const { return (S.D - S.tau0) / crack_area(); }
@@ -753,7 +800,10 @@ struct Engine : EngineBase {
     // timing
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
     size_t ev_used = 0;
-    std::vector<std::pair<int, double>> ev_meta;  // (mechanics projection pass?, bytes moved)
+    // per launch: kernel class (1 k_axis, 2 k_x_fwd, 3 k_x_inv, 4 k_x_mid, 5 k_pointwise), mechanics
+    // projection pass?, algorithmic bytes and FFT flops
+    struct EvMeta { int kind; int proj; double bytes, flops; };
+    std::vector<EvMeta> ev_meta;
     double bytes_mech_axis = 0.0;
     std::map<const void *, size_t> smem_set;
     // CUDA graphs of one iteration chunk, keyed by (solver kind, solution buffer, coefficient
@@ -883,12 +933,14 @@ struct Engine : EngineBase {
     explicit Engine(const rve_config &c) {
         cfg = c;
         if (kSingle) {
-            // FP32 field arithmetic: tolerances below what single-precision operators resolve
-            // are raised (the refinement loops then converge on the true residual).
-            cfg.tol_mech = std::max(cfg.tol_mech, 1e-6);
-            cfg.tol_dmg = std::max(cfg.tol_dmg, 1e-6);
-            cfg.tol_root = std::max(cfg.tol_root, 1e-6);
-            cfg.tol_stag = std::max(cfg.tol_stag, 1e-5);
+            // FP32 field arithmetic. The equilibrium is refined on its FP64 residual with an FP64
+            // solution, so its tolerance can go far below the FP32 rounding level; the damage
+            // solve, the control root and the staggered test see FP32 fields and keep floors
+            // at what those resolve.
+            cfg.tol_mech = std::max(cfg.tol_mech, 1e-13);
+            cfg.tol_dmg = std::max(cfg.tol_dmg, 1e-8);
+            cfg.tol_root = std::max(cfg.tol_root, 1e-9);
+            cfg.tol_stag = std::max(cfg.tol_stag, 1e-8);
         }
         D = c.dim;
         NS = D == 2 ? 3 : 6;
@@ -906,8 +958,10 @@ struct Engine : EngineBase {
         g.Nh = (long long)g.Px * g.ny * g.nz;
         g.invN = 1.0 / (double)g.N;
         N = g.N;
+        if (const char *aws = std::getenv("PFF_AXIS_WARPS")) aw = std::max(1, std::min(16, std::atoi(aws)));
         if (c.stream) st = (cudaStream_t)c.stream;
         else { CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own_stream = true; }
+        CK(axis_twiddles_init());  // constant-bank twiddles of the column passes (this device)
         try {
             gid = alloc<int>(N); gid0 = alloc<int>(N);
             phi = alloc<T>(N); phi_trial = alloc<T>(N); phi_cur = alloc<T>(N); H = alloc<T>(N); Hcur = alloc<T>(N);
@@ -990,13 +1044,14 @@ struct Engine : EngineBase {
     }
     std::vector<int> tile_candidates(int L) const {
         std::vector<int> v;
-        const int TL = L / 4;
         const int NM = std::max(NS, D);
         for (int cw = 1; cw <= 16; cw *= 2) {
-            const size_t sm = (size_t)NM * cw * L * sizeof(C);
-            if (cw * TL >= 32 && cw * TL <= 512 && sm <= 200 * 1024) v.push_back(cw);
+            int th;
+            size_t sm;
+            axis_shape<C>(L, NM, cw, th, sm);
+            if (sm <= 200 * 1024) v.push_back(cw);
         }
-        if (v.empty()) v.push_back(L >= 4 ? std::max(1, std::min(16, 128 / std::max(TL, 1))) : 2);
+        if (v.empty()) v.push_back(1);
         return v;
     }
     float time_tiles(int cy, int cz) {
@@ -1079,6 +1134,9 @@ struct Engine : EngineBase {
         allocs.clear();
         if (h_sc) cudaFreeHost(h_sc);
         h_sc = nullptr;
+        if (ev_ready) cudaEventDestroy(ev_ready);
+        if (ev_finished) cudaEventDestroy(ev_finished);
+        ev_ready = ev_finished = nullptr;
         if (own_stream && st) cudaStreamDestroy(st);
         st = nullptr;
     }
@@ -1099,29 +1157,104 @@ struct Engine : EngineBase {
             smem_set[key] = bytes;
         }
     }
-    void xcfg(int &threads, int &blocks, size_t &smem1) const {
+    // Events around one launch while timing is on (returns the end event to record after it).
+    cudaEvent_t tbeg(int kind, int proj, double bytes, double flops) {
+        if (!timing) return nullptr;
+        if (ev_used == ev_pool.size()) {
+            cudaEvent_t a, b;
+            CK(cudaEventCreate(&a)); CK(cudaEventCreate(&b));
+            ev_pool.push_back({a, b});
+        }
+        if (ev_meta.size() < ev_pool.size()) ev_meta.resize(ev_pool.size());
+        ev_meta[ev_used] = EvMeta{kind, proj, bytes, flops};
+        CK(cudaEventRecord(ev_pool[ev_used].first, st));
+        return ev_pool[ev_used++].second;
+    }
+    void tend(cudaEvent_t e) { if (e) CK(cudaEventRecord(e, st)); }
+    // FFT flops of NC transforms of the x rows (two real rows per complex line of nx points).
+    double xflops(int nc) const { return (double)nc * 0.5 * (double)g.ny * g.nz * 5.0 * g.nx * g.lx; }
+    // Algorithmic bytes of an x pass: nc_spec half-spectrum components and RW field words per voxel.
+    template <typename U = T> double xbytes(int nc_spec, int rw) const {
+        return (double)nc_spec * (g.nx / 2 + 1) * (double)g.ny * g.nz * sizeof(typename cplx_of<U>::type) +
+               (double)rw * N * sizeof(T);
+    }
+    // Spectral buffer, twiddles and frequency tables of the transforms in precision U: the
+    // engine's own for U = T; for U = double in the FP32 engine, a second set used by the FP64
+    // residual passes of the iterative refinement (allocated on first use).
+    typedef typename cplx_of<double>::type C64;
+    C64 *spec64 = nullptr;
+    std::map<int, C64 *> tw64;
+    double *xi64_x = nullptr, *xi64_y = nullptr, *xi64_z = nullptr;
+    template <typename U> typename cplx_of<U>::type *spec_of() {
+        if constexpr (std::is_same<U, T>::value) return spec;
+        else return spec64;
+    }
+    template <typename U> const typename cplx_of<U>::type *tw_of(int L) {
+        if constexpr (std::is_same<U, T>::value) return tw[L];
+        else return tw64[L];
+    }
+    XiTab<double> xitab64() const { return XiTab<double>{xi64_x, xi64_y, xi64_z}; }
+    void ensure_spectral64() {
+        if (spec64) return;
+        spec64 = alloc<C64>((size_t)std::max(NS, D) * (size_t)(((g.nx / 2 + 1 + 15) / 16) * 16) * g.ny * g.nz);
+        for (int L : {g.nx, g.ny, g.nz}) {
+            if (L < 4 || tw64.count(L)) continue;
+            std::vector<C64> h(L);
+            for (int m2 = 0; m2 < L; ++m2) {
+                long double a = -2.0L * 3.14159265358979323846264338327950288L * (long double)m2 / (long double)L;
+                h[m2].x = (double)std::cos(a);
+                h[m2].y = (double)std::sin(a);
+            }
+            C64 *d = alloc<C64>(L);
+            CK(cudaMemcpyAsync(d, h.data(), L * sizeof(C64), cudaMemcpyHostToDevice, st));
+            tw64[L] = d;
+        }
+        auto xi_host = [](int n, int len, bool half) {
+            std::vector<double> v(len, 0.0);
+            const int lim = half ? n / 2 + 1 : n;
+            for (int k = 0; k < lim && k < len; ++k) {
+                const int kk = k <= n / 2 ? k : k - n;
+                v[k] = (2 * k == n) ? 0.0
+                                    : (double)(2.0L * 3.14159265358979323846264338327950288L * (long double)kk / (long double)n);
+            }
+            return v;
+        };
+        auto up = [&](const std::vector<double> &h) {
+            double *d = alloc<double>(h.size());
+            CK(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+            return d;
+        };
+        xi64_x = up(xi_host(g.nx, ((g.nx / 2 + 1 + 15) / 16) * 16, true));
+        xi64_y = up(xi_host(g.ny, g.ny, false));
+        xi64_z = up(xi_host(g.nz, g.nz, false));
+    }
+    template <typename U = T> void xcfg(int &threads, int &blocks, size_t &smem1) const {
         const int TL = g.nx / 4;
         const long long pairs = (long long)g.ny * g.nz / 2;
         int RP = std::max(1, 128 / TL);
         if (RP > pairs) RP = (int)pairs;
         threads = RP * TL;
         blocks = (int)(pairs / RP);
-        smem1 = (size_t)RP * g.nx * sizeof(C);
+        smem1 = (size_t)RP * g.nx * sizeof(typename cplx_of<U>::type);
     }
-    template <int NC, class Pro> void x_fwd(const Pro &pro, Scal *s) {
-        int th, bl; size_t sm; xcfg(th, bl, sm);
-        auto k = k_x_fwd<T, NC, Pro>;
+    template <int NC, class Pro, typename U = T> void x_fwd(const Pro &pro, Scal *s) {
+        int th, bl; size_t sm; xcfg<U>(th, bl, sm);
+        auto k = k_x_fwd<U, NC, Pro>;
         prep_smem(k, sm * NC);
-        k<<<bl, th, sm * NC, st>>>(g, pro, spec, tw[g.nx], partials, s);
+        cudaEvent_t e = tbeg(2, 0, xbytes<U>(NC, rw_words<Pro>()), xflops(NC));
+        k<<<bl, th, sm * NC, st>>>(g, pro, spec_of<U>(), tw_of<U>(g.nx), partials, s);
         CK(cudaGetLastError());
+        tend(e);
         ++launches;
     }
-    template <int NC, class Epi> void x_inv(const Epi &epi, Scal *s) {
-        int th, bl; size_t sm; xcfg(th, bl, sm);
-        auto k = k_x_inv<T, NC, Epi>;
+    template <int NC, class Epi, typename U = T> void x_inv(const Epi &epi, Scal *s) {
+        int th, bl; size_t sm; xcfg<U>(th, bl, sm);
+        auto k = k_x_inv<U, NC, Epi>;
         prep_smem(k, sm * NC);
-        k<<<bl, th, sm * NC, st>>>(g, spec, epi, tw[g.nx], partials, s);
+        cudaEvent_t e = tbeg(3, 0, xbytes<U>(NC, rw_words<Epi>()), xflops(NC));
+        k<<<bl, th, sm * NC, st>>>(g, spec_of<U>(), epi, tw_of<U>(g.nx), partials, s);
         CK(cudaGetLastError());
+        tend(e);
         ++launches;
     }
     template <int NC, class Mid> void x_mid(const Mid &mid, Scal *s) { x_mid2<NC, NC>(mid, s); }
@@ -1129,38 +1262,42 @@ struct Engine : EngineBase {
         int th, bl; size_t sm; xcfg(th, bl, sm);
         auto k = k_x_mid<T, NCI, NCO, Mid>;
         prep_smem(k, sm * NCI);
+        cudaEvent_t e = tbeg(4, 0, xbytes(NCI + NCO, rw_words<Mid>()), xflops(NCI + NCO));
         k<<<bl, th, sm * NCI, st>>>(g, spec, mid, tw[g.nx], s);
         CK(cudaGetLastError());
+        tend(e);
         ++launches;
     }
-    template <int NCI, int NCO, int MODE, class Op> void axis(int ax, const Op &op, Scal *s, bool timed = false) {
+    template <int NCI, int NCO, int MODE, class Op, typename U = T>
+    void axis(int ax, const Op &op, Scal *s, bool timed = false) {
+        typedef typename cplx_of<U>::type CU;
         const int L = ax == 1 ? g.ny : g.nz;
-        const int TL = L / 4;
-        const int CW = ax == 1 ? cw_y : cw_z;
-        dim3 grid(g.Px / CW, ax == 1 ? g.nz : g.ny);
+        int CW = ax == 1 ? cw_y : cw_z;
         const int NM = NCI > NCO ? NCI : NCO;
-        const size_t sm = (size_t)NM * CW * L * sizeof(C);
-        auto k = k_axis<T, NCI, NCO, MODE, Op>;
-        prep_smem(k, sm);
-        cudaEvent_t e1 = nullptr, e2 = nullptr;
-        if (timing) {
-            // every column pass is timed; `timed` marks the mechanics projection pass. Bytes: the
-            // NCI components read and the components written, over the whole half spectrum.
-            if (ev_used == ev_pool.size()) {
-                cudaEvent_t a, b;
-                CK(cudaEventCreate(&a)); CK(cudaEventCreate(&b));
-                ev_pool.push_back({a, b});
-            }
-            const int nout = MODE == AX_FWD_OP_INV ? NCO : NCI;
-            if (ev_meta.size() < ev_pool.size()) ev_meta.resize(ev_pool.size());
-            ev_meta[ev_used] = {timed ? 1 : 0, (double)(NCI + nout) * (double)g.Nh * sizeof(C)};
-            e1 = ev_pool[ev_used].first; e2 = ev_pool[ev_used].second; ++ev_used;
-            CK(cudaEventRecord(e1, st));
+        int threads;
+        size_t sm;
+        axis_shape<CU>(L, NM, CW, threads, sm, aw);
+        // FP64 passes of the FP32 engine: halve the tuned width until the tile fits (Px stays a
+        // multiple of the narrower width)
+        while (sm > 200 * 1024 && CW > 1) {
+            CW >>= 1;
+            axis_shape<CU>(L, NM, CW, threads, sm, aw);
         }
-        k<<<grid, CW * TL, sm, st>>>(g, ax, spec, spec, op, tw[L], s);
+        dim3 grid(g.Px / CW, ax == 1 ? g.nz : g.ny);
+        auto k = axis_kernel<U, NCI, NCO, MODE, Op>(L);
+        prep_smem(k, sm);
+        // timing: `timed` marks the mechanics projection pass. Bytes: the NCI components read and
+        // the components written over the half spectrum (the nx/2 + 1 columns, no tile padding);
+        // flops: 5 L log2 L per transformed column and component.
+        const int nout = MODE == AX_FWD_OP_INV ? NCO : NCI;
+        const int ntr = MODE == AX_FWD_OP_INV ? NCI + NCO : NCI;
+        const double cols = (double)(g.nx / 2 + 1) * (ax == 1 ? g.nz : g.ny);
+        cudaEvent_t e = tbeg(1, timed ? 1 : 0, (double)(NCI + nout) * cols * L * sizeof(CU),
+                             (double)ntr * cols * 5.0 * L * (ax == 1 ? g.ly : g.lz));
+        k<<<grid, threads, sm, st>>>(g, ax, CW, spec_of<U>(), spec_of<U>(), op, tw_of<U>(L), s);
         CK(cudaGetLastError());
+        tend(e);
         ++launches;
-        if (e2) CK(cudaEventRecord(e2, st));
     }
     // Grid of the pointwise kernels. Those that reduce pay a fixed per-CTA cost (block reduction,
     // fence, atomic ticket), which dominated at one voxel per thread; they run 2 CTAs per SM with
@@ -1177,34 +1314,280 @@ struct Engine : EngineBase {
         return bl > cap ? cap : bl;
     }
     template <class F> void pointwise(const F &f, Scal *s) {
+        cudaEvent_t e = tbeg(5, 0, (double)rw_words<F>() * N * sizeof(T), 0.0);
         k_pointwise<F><<<(int)pw_blocks<F>(N), 256, 0, st>>>(N, f, partials, s);
         CK(cudaGetLastError());
+        tend(e);
         ++launches;
     }
     // Spectral passes between the x passes: 2D one y pass; 3D y, z (with the operator), y. A 3D
     // grid one voxel thick (nz = 1, the plates of Sec. 5) has xi_z = 0 everywhere and needs no z
     // transform: the operator runs in the y pass, as in 2D, with all NS components.
-    template <int NCI, int NCO, class Op> void spectral(const Op &op, Scal *s, bool timed = false) {
+    template <int NCI, int NCO, class Op, typename U = T> void spectral(const Op &op, Scal *s, bool timed = false) {
+        typedef typename cplx_of<U>::type CU;
         if (D == 2 || g.nz == 1) {
-            axis<NCI, NCO, AX_FWD_OP_INV>(1, op, s, timed);
+            axis<NCI, NCO, AX_FWD_OP_INV, Op, U>(1, op, s, timed);
         } else {
-            OpNone<C> nop{op.skip_if_done};
-            axis<NCI, NCI, AX_FWD>(1, nop, s, timed);
-            axis<NCI, NCO, AX_FWD_OP_INV>(2, op, s, timed);
-            axis<NCO, NCO, AX_INV>(1, nop, s, timed);
+            OpNone<CU> nop{op.skip_if_done};
+            axis<NCI, NCI, AX_FWD, OpNone<CU>, U>(1, nop, s, timed);
+            axis<NCI, NCO, AX_FWD_OP_INV, Op, U>(2, op, s, timed);
+            axis<NCO, NCO, AX_INV, OpNone<CU>, U>(1, nop, s, timed);
         }
     }
     void read_sc(Scal *s) {
         CK(cudaMemcpyAsync(h_sc, s, sizeof(Scal), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
     }
-    void init_sc(Scal *s, double tol, int maxit, double abar = 0.0, double bbar = 0.0) {
-        k_init_scal<<<1, 1, 0, st>>>(s, tol * tol, maxit, abar, bbar);
+    void init_sc(Scal *s, double tol, int maxit, double abar = 0.0, double bbar = 0.0, double eta = 0.0) {
+        k_init_scal<<<1, 1, 0, st>>>(s, tol * tol, maxit, abar, bbar, eta * eta);
         ++launches;
     }
 
+    // ---- batched launches (rve_step_batch): one launch per pass for several RVEs of this grid -------
+    template <class F>
+    static SlotArgs<F> slot_args(const std::vector<Engine *> &es, const std::vector<F> &fs, const std::vector<Scal *> &scs) {
+        SlotArgs<F> a;
+        for (size_t i = 0; i < es.size(); ++i) {
+            a.a[i].f = fs[i];
+            a.a[i].spec = es[i]->spec;
+            a.a[i].partials = es[i]->partials;
+            a.a[i].sc = scs[i];
+        }
+        return a;
+    }
+    template <int NC, class Pro>
+    void x_fwd_b(const std::vector<Engine *> &es, const std::vector<Pro> &fs, const std::vector<Scal *> &scs,
+                 cudaStream_t s) {
+        int th, bl; size_t sm; xcfg(th, bl, sm);
+        auto k = k_x_fwd_b<T, NC, Pro>;
+        prep_smem(k, sm * NC);
+        k<<<dim3(bl, 1, (unsigned)es.size()), th, sm * NC, s>>>(g, slot_args(es, fs, scs), tw[g.nx]);
+    }
+    template <int NC, class Epi>
+    void x_inv_b(const std::vector<Engine *> &es, const std::vector<Epi> &fs, const std::vector<Scal *> &scs,
+                 cudaStream_t s) {
+        int th, bl; size_t sm; xcfg(th, bl, sm);
+        auto k = k_x_inv_b<T, NC, Epi>;
+        prep_smem(k, sm * NC);
+        k<<<dim3(bl, 1, (unsigned)es.size()), th, sm * NC, s>>>(g, slot_args(es, fs, scs), tw[g.nx]);
+    }
+    template <int NCI, int NCO, class Mid>
+    void x_mid_b(const std::vector<Engine *> &es, const std::vector<Mid> &fs, const std::vector<Scal *> &scs,
+                 cudaStream_t s) {
+        int th, bl; size_t sm; xcfg(th, bl, sm);
+        auto k = k_x_mid_b<T, NCI, NCO, Mid>;
+        prep_smem(k, sm * NCI);
+        k<<<dim3(bl, 1, (unsigned)es.size()), th, sm * NCI, s>>>(g, slot_args(es, fs, scs), tw[g.nx]);
+    }
+    template <int NCI, int NCO, int MODE, class Op>
+    void axis_b(int ax, const std::vector<Engine *> &es, const std::vector<Op> &fs, const std::vector<Scal *> &scs,
+                cudaStream_t s) {
+        const int L = ax == 1 ? g.ny : g.nz;
+        const int CW = ax == 1 ? cw_y : cw_z;
+        const int NM = NCI > NCO ? NCI : NCO;
+        int threads;
+        size_t sm;
+        axis_shape<C>(L, NM, CW, threads, sm, aw);
+        auto k = axis_kernel_b<T, NCI, NCO, MODE, Op>(L);
+        prep_smem(k, sm);
+        k<<<dim3(g.Px / CW, ax == 1 ? g.nz : g.ny, (unsigned)es.size()), threads, sm, s>>>(g, ax, CW,
+                                                                                         slot_args(es, fs, scs), tw[L]);
+    }
+    template <int NCI, int NCO, class Op>
+    int spectral_b(const std::vector<Engine *> &es, const std::vector<Op> &fs, const std::vector<Scal *> &scs,
+                   cudaStream_t s) {
+        if (D == 2 || g.nz == 1) {
+            axis_b<NCI, NCO, AX_FWD_OP_INV, Op>(1, es, fs, scs, s);
+            return 1;
+        }
+        std::vector<OpNone<C>> nops(es.size(), OpNone<C>{true});
+        axis_b<NCI, NCI, AX_FWD, OpNone<C>>(1, es, nops, scs, s);
+        axis_b<NCI, NCO, AX_FWD_OP_INV, Op>(2, es, fs, scs, s);
+        axis_b<NCO, NCO, AX_INV, OpNone<C>>(1, es, nops, scs, s);
+        return 3;
+    }
+    // One iteration loop of a solve handed to the Batcher: the equilibrium CG (ProCGCG -> projection
+    // -> EpiCGCG) or the damage PCG (ProPCGCG -> preconditioner + gradient -> flux -> divergence ->
+    // EpiPCGCG), each RVE with its own functors.
+    cudaEvent_t ev_ready = nullptr, ev_finished = nullptr;
+    template <class Q> void batch_request(Q &q) {
+        if (!ev_ready) {
+            CK(cudaEventCreateWithFlags(&ev_ready, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&ev_finished, cudaEventDisableTiming));
+        }
+        q.e = this;
+        q.sc = sc;
+        q.h_sc = h_sc;
+        q.slot_stream = st;
+        q.ready = ev_ready;
+        q.finished = ev_finished;
+        q.launch_counter = &launches;
+        q.launch = &Q::run_iters;
+        batcher->run(&q);
+        if (q.err != cudaSuccess) throw CudaError{q.err, "batched solve"};
+    }
+    template <int NSx> struct MechLoop : LoopReq {
+        Engine *e = nullptr;
+        ProCGCG<T, NSx> dir;
+        OpProj<C, NSx> proj;
+        EpiCGCG<T, NSx> eq;
+        static void run_iters(std::vector<LoopReq *> &grp, cudaStream_t s, int iters) {
+            const size_t n = grp.size();
+            std::vector<Engine *> es(n);
+            std::vector<ProCGCG<T, NSx>> ds(n);
+            std::vector<OpProj<C, NSx>> ps(n);
+            std::vector<EpiCGCG<T, NSx>> qs(n);
+            std::vector<Scal *> scs(n);
+            for (size_t i = 0; i < n; ++i) {
+                auto *r = static_cast<MechLoop *>(grp[i]);
+                es[i] = r->e; ds[i] = r->dir; ps[i] = r->proj; qs[i] = r->eq; scs[i] = r->sc;
+            }
+            Engine *e0 = es[0];
+            long k = 0;
+            for (int it = 0; it < iters; ++it) {
+                e0->template x_fwd_b<NSx>(es, ds, scs, s);
+                k += e0->template spectral_b<NSx, NSx>(es, ps, scs, s);
+                e0->template x_inv_b<NSx>(es, qs, scs, s);
+                k += 2;
+            }
+            *grp[0]->launch_counter += k;
+        }
+    };
+    template <int Dx> struct DmgLoop : LoopReq {
+        Engine *e = nullptr;
+        ProPCGCG<T> pdir;
+        OpPrecGrad<C, Dx> pgrad;
+        MidFluxU<T, Dx> fluxu;
+        OpDiv<C, Dx> divo;
+        EpiPCGCG<T> ew;
+        static void run_iters(std::vector<LoopReq *> &grp, cudaStream_t s, int iters) {
+            const size_t n = grp.size();
+            std::vector<Engine *> es(n);
+            std::vector<ProPCGCG<T>> a(n);
+            std::vector<OpPrecGrad<C, Dx>> b(n);
+            std::vector<MidFluxU<T, Dx>> c(n);
+            std::vector<OpDiv<C, Dx>> d(n);
+            std::vector<EpiPCGCG<T>> w(n);
+            std::vector<Scal *> scs(n);
+            for (size_t i = 0; i < n; ++i) {
+                auto *r = static_cast<DmgLoop *>(grp[i]);
+                es[i] = r->e; a[i] = r->pdir; b[i] = r->pgrad; c[i] = r->fluxu; d[i] = r->divo; w[i] = r->ew;
+                scs[i] = r->sc;
+            }
+            Engine *e0 = es[0];
+            long k = 0;
+            for (int it = 0; it < iters; ++it) {
+                e0->template x_fwd_b<1>(es, a, scs, s);
+                k += e0->template spectral_b<1, Dx + 1>(es, b, scs, s);
+                e0->template x_mid_b<Dx + 1, Dx>(es, c, scs, s);
+                k += e0->template spectral_b<Dx, 1>(es, d, scs, s);
+                e0->template x_inv_b<1>(es, w, scs, s);
+                k += 3;
+            }
+            *grp[0]->launch_counter += k;
+        }
+    };
+
     // ---- mechanics (a1-a5) ---------------------------------------------------------------------
+    // ---- FP32 path: mixed-precision iterative refinement of the equilibrium ---------------------
+    // x (the unit-load fluctuation) is kept in FP64 (mx64). Each pass evaluates the true residual
+    // r = -P[g C : (f + x)] with FP64 transforms and tables, then runs the FP32 single-reduction
+    // CG on the correction A d = r (d in md) until <r, r> drops by eta^2 or meets the tolerance,
+    // and adds the compatible part P[d] of d to x in FP64 (EpiAddCorrection says why). The solve
+    // ends at the first pass whose FP64 residual meets the tolerance. mx then holds x rounded to
+    // FP32 for the consumers of the fluctuation.
+    double *mx64 = nullptr, *Cm64 = nullptr;
+    T *md = nullptr;
+    bool mx64_ok = false;
+    // inner reduction of each refinement pass; PFF_REFINE_ETA overrides it (tuning)
+    double refine_eta = std::getenv("PFF_REFINE_ETA") ? std::atof(std::getenv("PFF_REFINE_ETA")) : 1e-4;
+    void ensure_mx64() {
+        if (!mx64) mx64 = alloc<double>((size_t)NS * N);
+        if (!mx64_ok) {
+            k_copy_cast<T><<<(int)((NS * N + 255) / 256), 256, 0, st>>>(NS * N, mx, mx64);
+            CK(cudaGetLastError());
+            ++launches;
+            mx64_ok = true;
+        }
+    }
+    template <int NSx> int mech_solve_refined(const T *phi_in, int &iters) {
+        ensure_spectral64();
+        ensure_mx64();
+        if (!md) md = alloc<T>((size_t)NS * N);
+        if (!mw) mw = alloc<T>((size_t)NS * N);
+        CK(cudaMemsetAsync(md, 0, sizeof(T) * NS * N, st));
+        MechBase<T, NSx> mb{Cm, gid, phi_in, (T)cfg.k_res, N, true};
+        ProStressTotal64<NSx> pro64{true, Cm64, gid, (const float *)phi_in, cfg.k_res, mx64, {}, N};
+        for (int a = 0; a < NSx; ++a) pro64.f[a] = fM[a];
+        OpProj<C64, NSx> proj64{true, xitab64()};
+        OpProj<C, NSx> proj{true, xitab()};
+        ProCGCG<T, NSx> dir;
+        (MechBase<T, NSx> &)dir = mb;
+        dir.x = md; dir.r = mr; dir.p = mp; dir.s = mq; dir.w = mw; dir.scr = sc;
+        EpiCGCG<T, NSx> eq{true, mw, mr, N};
+        const int chunk = timing ? 1 : 8;
+        iters = 0;
+        bool converged = false;
+        for (int pass = 0; pass < 16 && !converged; ++pass) {
+            init_sc(sc, cfg.tol_mech, std::max(1, cfg.max_mech_iters - iters), 0.0, 0.0, refine_eta);
+            x_fwd<NSx, ProStressTotal64<NSx>, double>(pro64, sc);
+            spectral<NSx, NSx, OpProj<C64, NSx>, double>(proj64, sc, true);
+            x_inv<NSx, EpiMechInit64<NSx>, double>(EpiMechInit64<NSx>{true, (float *)mr, N}, sc);
+            auto iter_body = [&] {
+                x_fwd<NSx>(dir, sc);
+                spectral<NSx, NSx>(proj, sc, true);
+                x_inv<NSx>(eq, sc);
+            };
+            if (batcher) {
+                MechLoop<NSx> q;
+                q.dir = dir; q.proj = proj; q.eq = eq;
+                batch_request(q);
+            } else if (run_loop(1, phi_in, nullptr, sc, iter_body)) {
+                read_sc(sc);
+                count_loop(1, phi_in, nullptr, h_sc->iters);
+            } else {
+                for (;;) {
+                    run_chunk(1, phi_in, nullptr, [&] {
+                        for (int c = 0; c < chunk; ++c) iter_body();
+                    });
+                    read_sc(sc);
+                    if (h_sc->done) break;
+                }
+            }
+            iters += h_sc->iters;
+            if (h_sc->flag & FLAG_NONFINITE) return fail(RVE_EBREAKDOWN, "equilibrium CG: non-finite scalar");
+            if (h_sc->flag) {
+                // FP32 CG breakdown (<p, A p> <= 0 from rounding in a nearly singular system):
+                // on a residual already at the rounding floor (within 100 x the tolerance, FP64-
+                // verified at the start of this pass) the verified x is kept; otherwise the
+                // correction gathered before the breakdown is added and the next pass restarts
+                // from the FP64 residual (the pass cap bounds this)
+                if (h_sc->rr0 <= 1e4 * h_sc->tol2 * h_sc->scale2) {
+                    CK(cudaMemsetAsync(md, 0, sizeof(T) * NS * N, st));
+                    converged = true;
+                    break;
+                }
+            } else {
+                if (h_sc->iters == 0) { converged = true; break; }  // the FP64 residual met the tolerance
+                if (!(h_sc->rr <= h_sc->tol2 * h_sc->scale2) && !(h_sc->rr <= h_sc->eta2 * h_sc->rr0))
+                    return fail(RVE_ENOCONV, "equilibrium CG: iteration cap");
+            }
+            x_fwd<NSx>(ProCorrection<T, NSx>{false, md, N}, sc2);
+            spectral<NSx, NSx>(OpProj<C, NSx>{false, xitab()}, sc2);
+            x_inv<NSx>(EpiAddCorrection<T, NSx>{false, mx64, md, N}, sc2);
+        }
+        if (!converged) return fail(RVE_ENOCONV, "equilibrium: iterative refinement did not reach the tolerance");
+        k_cast_copy<T><<<(int)((NS * N + 255) / 256), 256, 0, st>>>(NS * N, mx64, mx);
+        CK(cudaGetLastError());
+        ++launches;
+        PwPsi1<T, NSx> ps{false, Cm, mx, gid, psi1, {}, N};
+        for (int a = 0; a < NSx; ++a) ps.f[a] = (T)fM[a];
+        pointwise(ps, sc);
+        return RVE_OK;
+    }
+
     template <int NSx> int mech_solve_t(const T *phi_in, int &iters) {
+        if constexpr (kSingle) return mech_solve_refined<NSx>(phi_in, iters);
         MechBase<T, NSx> mb{Cm, gid, phi_in, (T)cfg.k_res, N, true};
         ProStressTotal<T, NSx> pro;
         (MechBase<T, NSx> &)pro = mb;
@@ -1238,7 +1621,11 @@ struct Engine : EngineBase {
                 spectral<NSx, NSx>(proj, sc, true);
                 x_inv<NSx>(eq, sc);
             };
-            if (run_loop(1, phi_in, nullptr, sc, iter_body)) {
+            if (batcher) {
+                MechLoop<NSx> q;
+                q.dir = dir; q.proj = proj; q.eq = eq;
+                batch_request(q);
+            } else if (run_loop(1, phi_in, nullptr, sc, iter_body)) {
                 read_sc(sc);
                 count_loop(1, phi_in, nullptr, h_sc->iters);
             } else {
@@ -1326,6 +1713,7 @@ struct Engine : EngineBase {
             if (iters >= cfg.max_mech_iters) return fail(RVE_ENOCONV, "split equilibrium: CG iteration cap");
             if (newton == 99) return fail(RVE_ENOCONV, "split equilibrium: Newton did not converge in 100 steps");
         }
+        mx64_ok = false;  // the split solve updates mx itself
         PwPsi1Split<T> ps{false, mx, lamT, muT, gid, psi1, {}, N};
         for (int a = 0; a < 3; ++a) ps.f[a] = (T)fM[a];
         pointwise(ps, sc);
@@ -1380,7 +1768,11 @@ struct Engine : EngineBase {
                 spectral<Dx, 1>(divo, sc);
                 x_inv<1>(ew, sc);
             };
-            if (run_loop(3, x, co.Ktab, sc, iter_body)) {
+            if (batcher) {
+                DmgLoop<Dx> q;
+                q.pdir = pdir; q.pgrad = pgrad; q.fluxu = fluxu; q.divo = divo; q.ew = ew;
+                batch_request(q);
+            } else if (run_loop(3, x, co.Ktab, sc, iter_body)) {
                 read_sc(sc);
                 count_loop(3, x, co.Ktab, h_sc->iters);
             } else {
@@ -1515,6 +1907,28 @@ struct Engine : EngineBase {
         k_build_tables<T><<<(G2 + 63) / 64, 64, 0, st>>>(G, D, dCc, dR, dGc, dcn, dbe, cfg.ell, m->crack_stiffness, Cm,
                                                           acoef, Ktab, GcTab, Atab, acoefC, KtabC, lamT, muT);
         ++launches;
+        if constexpr (kSingle) {
+            // FP64 copy of the stiffness table for the FP64 residual of the refinement (the other
+            // FP64 tables are built and dropped)
+            if (Cm64) {
+                cudaFree(Cm64);
+                allocs.erase(std::remove(allocs.begin(), allocs.end(), (void *)Cm64), allocs.end());
+            }
+            Cm64 = alloc<double>((size_t)G2 * NS * NS);
+            double *t64;
+            const size_t per = 1 + 6 + 1 + 6 + 1 + 6 + 1 + 1;
+            CK(cudaMalloc(&t64, sizeof(double) * per * G2));
+            double *q = t64;
+            double *a1 = q; q += G2; double *a2 = q; q += 6 * G2; double *a3 = q; q += G2; double *a4 = q; q += 6 * G2;
+            double *a5 = q; q += G2; double *a6 = q; q += 6 * G2; double *a7 = q; q += G2; double *a8 = q;
+            k_build_tables<double><<<(G2 + 63) / 64, 64, 0, st>>>(G, D, dCc, dR, dGc, dcn, dbe, cfg.ell,
+                                                                   m->crack_stiffness, Cm64, a1, a2, a3, a4, a5, a6,
+                                                                   a7, a8);
+            CK(cudaGetLastError());
+            ++launches;
+            CK(cudaStreamSynchronize(st));
+            CK(cudaFree(t64));
+        }
         const int cx0 = ((m->crack_x0 % g.nx) + g.nx) % g.nx;
         k_crack_setup<<<(int)((N + 255) / 256), 256, 0, st>>>(N, g.nx, g.ny, gid0, G, m->crack_kind, m->crack_row, cx0,
                                                               m->crack_len, gid, phi_disc);
@@ -1530,6 +1944,7 @@ struct Engine : EngineBase {
         if (dbe) CK(cudaFree(dbe));
         // enriched initial crack
         CK(cudaMemsetAsync(mx, 0, sizeof(T) * NS * N, st));
+        mx64_ok = false;
         CK(cudaMemsetAsync(eps_com, 0, sizeof(double) * NS * N, st));
         CK(cudaMemsetAsync(psi1, 0, sizeof(T) * N, st));
         double tau0 = 0.0, Gamma0 = 0.0;
@@ -2190,12 +2605,17 @@ struct Engine : EngineBase {
     // checkpoint payload: phi, H, psi_ini, strain fluctuation (field precision), committed strain
     // (FP64), and the control search's slope memory (so a restored run repeats the same iterates)
     size_t state_bytes() const override {
-        return (size_t)N * sizeof(T) * (3 + NS) + (size_t)NS * N * sizeof(double) + sizeof(double);
+        return (size_t)N * sizeof(T) * (3 + NS) + (size_t)NS * N * sizeof(double) * (kSingle ? 2 : 1) + sizeof(double);
     }
     void save_state(char *p) override {
         const void *src[5] = {phi, H, psi_ini, mx, eps_com};
         const size_t sz[5] = {N * sizeof(T), N * sizeof(T), N * sizeof(T), NS * N * sizeof(T), NS * N * sizeof(double)};
         for (int i = 0; i < 5; ++i) { CK(cudaMemcpyAsync(p, src[i], sz[i], cudaMemcpyDeviceToHost, st)); p += sz[i]; }
+        if (kSingle) {  // the FP64 fluctuation of the refinement, so that a restore continues bit for bit
+            ensure_mx64();
+            CK(cudaMemcpyAsync(p, mx64, NS * N * sizeof(double), cudaMemcpyDeviceToHost, st));
+            p += NS * N * sizeof(double);
+        }
         std::memcpy(p, &root_slope, sizeof(double));
         CK(cudaStreamSynchronize(st));
     }
@@ -2203,26 +2623,36 @@ struct Engine : EngineBase {
         void *dst[5] = {phi, H, psi_ini, mx, eps_com};
         const size_t sz[5] = {N * sizeof(T), N * sizeof(T), N * sizeof(T), NS * N * sizeof(T), NS * N * sizeof(double)};
         for (int i = 0; i < 5; ++i) { CK(cudaMemcpyAsync(dst[i], p, sz[i], cudaMemcpyHostToDevice, st)); p += sz[i]; }
+        if (kSingle) {
+            if (!mx64) mx64 = alloc<double>((size_t)NS * N);
+            CK(cudaMemcpyAsync(mx64, p, NS * N * sizeof(double), cudaMemcpyHostToDevice, st));
+            p += NS * N * sizeof(double);
+            mx64_ok = true;
+        }
         std::memcpy(&root_slope, p, sizeof(double));
         CK(cudaMemcpyAsync(phi_trial, phi, N * sizeof(T), cudaMemcpyDeviceToDevice, st));
         CK(cudaStreamSynchronize(st));
     }
     void timing_reset() override { ev_used = 0; }
-    void timing_get(int kind, double &ms, long &n, double &bytes) override {
+    void timing_get(int kind, double &ms, long &n, double &bytes, double &flops) override {
         CK(cudaStreamSynchronize(st));
-        double tot = 0.0, by = 0.0;
+        double tot = 0.0, by = 0.0, fl = 0.0;
         long cnt = 0;
         for (size_t i = 0; i < ev_used; ++i) {
-            if (kind == 0 && !ev_meta[i].first) continue;
+            const EvMeta &m = ev_meta[i];
+            const bool take = kind == 0 ? m.proj != 0 : kind == 6 ? true : m.kind == kind;
+            if (!take) continue;
             float t = 0.f;
             CK(cudaEventElapsedTime(&t, ev_pool[i].first, ev_pool[i].second));
             tot += t;
-            by += ev_meta[i].second;
+            by += m.bytes;
+            fl += m.flops;
             ++cnt;
         }
         ms = tot;
         n = cnt;
         bytes = cnt ? by / (double)cnt : 0.0;
+        flops = cnt ? fl / (double)cnt : 0.0;
     }
 
     // ---- field access --------------------------------------------------------------------------
@@ -2276,7 +2706,10 @@ struct Engine : EngineBase {
         } else if (field == RVE_FIELD_FLUCT1 || field == RVE_FIELD_EPS) {
             if (n != nten) return RVE_EINVAL;
             CK(cudaMemcpyAsync(dtmp, host, n * sizeof(double), cudaMemcpyHostToDevice, st));
-            if (field == RVE_FIELD_FLUCT1) k_tensor_to_mandel<T><<<blocks, 256, 0, st>>>(N, D, dtmp, mx);
+            if (field == RVE_FIELD_FLUCT1) {
+                k_tensor_to_mandel<T><<<blocks, 256, 0, st>>>(N, D, dtmp, mx);
+                mx64_ok = false;
+            }
             else k_tensor_to_mandel<double><<<blocks, 256, 0, st>>>(N, D, dtmp, eps_com);
         } else {
             return RVE_EINVAL;
@@ -2286,297 +2719,8 @@ struct Engine : EngineBase {
     }
 };
 
+// Engine factories, one per field precision, each compiled in a translation unit of its own.
+EngineBase *make_engine_f64(const rve_config &c);
+EngineBase *make_engine_f32(const rve_config &c);
+
 }  // namespace pffeng
-
-using namespace pffeng;
-
-// ================================================================================================
-// C ABI
-// ================================================================================================
-struct rve_s {
-    rve_config cfg;
-    std::unique_ptr<EngineBase> e;
-};
-
-#define GUARD_BEGIN try {
-#define GUARD_END                                                                    \
-    }                                                                                \
-    catch (const CudaError &ce) {                                                    \
-        g_last_error = std::string(ce.what) + ": " + cudaGetErrorString(ce.e);       \
-        return RVE_ECUDA;                                                            \
-    }                                                                                \
-    catch (const StatusError &se) {                                                  \
-        g_last_error = se.msg;                                                       \
-        return se.code;                                                              \
-    }                                                                                \
-    catch (...) {                                                                    \
-        g_last_error = "unknown error";                                              \
-        return RVE_ECUDA;                                                            \
-    }
-
-extern "C" {
-
-void rve_config_default(rve_config *c) {
-    std::memset(c, 0, sizeof(*c));
-    c->dim = 2;
-    c->n[0] = 64; c->n[1] = 64; c->n[2] = 1;
-    c->ell = 2.0;
-    c->k_res = 1e-6;
-    c->split = RVE_SPLIT_NONE;
-    c->precision = RVE_FP64;
-    c->history = 1;
-    c->f[1] = 1.0;
-    c->tol_mech = 1e-12;
-    c->tol_dmg = 1e-12;
-    c->tol_root = 1e-13;
-    c->tol_stag = 1e-10;
-    c->max_mech_iters = 20000;
-    c->max_dmg_iters = 20000;
-    c->max_root_evals = 200;
-    c->max_stag_iters = 300;
-    c->anderson_m = 5;
-    c->fracture_ratio = 0.01;
-    c->stream = nullptr;
-    c->solver = RVE_SOLVER_STAGGERED;
-}
-
-static bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
-
-int rve_config_validate(const rve_config *cfg) {
-    if (!cfg) return RVE_EINVAL;
-    if (cfg->dim != 2 && cfg->dim != 3) return RVE_EINVAL;
-    if (!pow2_in(cfg->n[0], 4, 1024) || !pow2_in(cfg->n[1], 4, 1024)) return RVE_EINVAL;
-    if (cfg->dim == 2 && cfg->n[2] != 1) return RVE_EINVAL;
-    if (cfg->dim == 3 && cfg->n[2] != 1 && !pow2_in(cfg->n[2], 4, 1024)) return RVE_EINVAL;
-    if ((long long)cfg->n[0] * cfg->n[1] * cfg->n[2] > (1LL << 24)) return RVE_EINVAL;
-    {
-        // the x passes reduce with full-warp shuffles: their CTAs need at least one whole warp
-        const int TL = cfg->n[0] / 4;
-        const long long pairs = (long long)cfg->n[1] * cfg->n[2] / 2;
-        const long long RP = std::min<long long>(std::max(1, 128 / TL), pairs);
-        if (RP * TL < 32) {
-            g_last_error = "grid too small: the x passes need (nx/4) * min(128/(nx/4), ny*nz/2) >= 32";
-            return RVE_EINVAL;
-        }
-    }
-    if (!(cfg->ell > 0) || cfg->k_res < 0 || cfg->anderson_m < 0 || cfg->anderson_m > 5) return RVE_EINVAL;
-    if (cfg->split != RVE_SPLIT_NONE && cfg->split != RVE_SPLIT_SPECTRAL) return RVE_EINVAL;
-    if (cfg->split == RVE_SPLIT_SPECTRAL && cfg->dim != 2) return RVE_EINVAL;  // split: plane strain only
-    if (cfg->solver != RVE_SOLVER_STAGGERED && cfg->solver != RVE_SOLVER_NEWTON) return RVE_EINVAL;
-    if (cfg->solver == RVE_SOLVER_NEWTON && cfg->split != RVE_SPLIT_NONE) return RVE_EINVAL;  // not linearised
-    if (cfg->solver == RVE_SOLVER_NEWTON && cfg->precision != RVE_FP64) {
-        // BiCGSTAB on the coupled single-precision system broke down before its tolerance
-        g_last_error = "the Newton solver runs in FP64 only";
-        return RVE_EINVAL;
-    }
-    if (cfg->precision != RVE_FP64 && cfg->precision != RVE_FP32R) return RVE_EINVAL;
-    return RVE_OK;
-}
-
-int rve_create(const rve_config *cfg, rve_handle *out) {
-    if (!cfg || !out) return RVE_EINVAL;
-    *out = nullptr;
-    if (int rc = rve_config_validate(cfg)) return rc;
-    GUARD_BEGIN
-    auto *h = new rve_s();
-    h->cfg = *cfg;
-    try {
-        if (cfg->precision == RVE_FP64) h->e.reset(new Engine<double>(*cfg));
-        else h->e.reset(new Engine<float>(*cfg));
-    } catch (...) {
-        delete h;
-        throw;
-    }
-    *out = h;
-    return RVE_OK;
-    GUARD_END
-}
-
-int set_microstructure(rve_handle h, const rve_micro *m) {
-    if (!h || !m) return RVE_EINVAL;
-    GUARD_BEGIN
-    h->e->crack_len_ = m->crack_kind == RVE_CRACK_NONE ? 0 : m->crack_len;
-    return h->e->set_micro(m);
-    GUARD_END
-}
-
-int step_dissipation(rve_handle h, double dtau, rve_step_result *out) {
-    if (!h) return RVE_EINVAL;
-    GUARD_BEGIN
-    return h->e->step(dtau, out);
-    GUARD_END
-}
-
-int effective_toughness(rve_handle h, double *g_eff) {
-    if (!h || !g_eff) return RVE_EINVAL;
-    if (!h->e->micro_set) return RVE_ESTATE;
-    if (!h->e->S.fractured) return RVE_ENOTFRACTURED;
-    *g_eff = h->e->toughness_value();
-    return RVE_OK;
-}
-
-int effective_toughness_functional(rve_handle h, double *g_eff) {
-    if (!h || !g_eff) return RVE_EINVAL;
-    if (!h->e->micro_set) return RVE_ESTATE;
-    if (!h->e->S.fractured) return RVE_ENOTFRACTURED;
-    *g_eff = h->e->toughness_functional_value();
-    return RVE_OK;
-}
-
-int rve_get_field(rve_handle h, int field, double *host, size_t n) {
-    if (!h || !host) return RVE_EINVAL;
-    GUARD_BEGIN
-    return h->e->get_field(field, host, n);
-    GUARD_END
-}
-
-int rve_set_field(rve_handle h, int field, const double *host, size_t n) {
-    if (!h || !host) return RVE_EINVAL;
-    GUARD_BEGIN
-    return h->e->set_field(field, host, n);
-    GUARD_END
-}
-
-int rve_get_scalars(rve_handle h, rve_scalars *s) {
-    if (!h || !s) return RVE_EINVAL;
-    *s = h->e->S;
-    return RVE_OK;
-}
-
-int rve_set_scalars(rve_handle h, const rve_scalars *s) {
-    if (!h || !s) return RVE_EINVAL;
-    h->e->S = *s;
-    return RVE_OK;
-}
-
-int rve_mech_solve(rve_handle h, int *iters) {
-    if (!h) return RVE_EINVAL;
-    if (!h->e->micro_set) return RVE_ESTATE;
-    GUARD_BEGIN
-    int it = 0;
-    int rc = h->e->mech_solve_committed(it);
-    if (iters) *iters = it;
-    return rc;
-    GUARD_END
-}
-
-int rve_damage_solve(rve_handle h, double E, double *Dv, int *iters) {
-    if (!h) return RVE_EINVAL;
-    if (!h->e->micro_set) return RVE_ESTATE;
-    GUARD_BEGIN
-    int it = 0;
-    double d = 0.0;
-    int rc = h->e->damage_eval_api(E, d, it);
-    if (Dv) *Dv = d;
-    if (iters) *iters = it;
-    return rc;
-    GUARD_END
-}
-
-int rve_dissipation(rve_handle h, const double *phi_host, double *Dv, double *Gv) {
-    if (!h || !phi_host) return RVE_EINVAL;
-    if (!h->e->micro_set) return RVE_ESTATE;
-    GUARD_BEGIN
-    double d = 0.0, gm = 0.0;
-    int rc = h->e->dissipation_host(phi_host, d, gm);
-    if (Dv) *Dv = d;
-    if (Gv) *Gv = gm;
-    return rc;
-    GUARD_END
-}
-
-// Checkpoint layout: rve_scalars | curve length | curve | raw device buffers (phi, H, psi_ini,
-// strain fluctuation in the handle's precision and Mandel layout, committed strain in FP64), so
-// a reload continues the load path bit-exactly.
-int rve_save(rve_handle h, void *buf, size_t *len) {
-    if (!h || !len) return RVE_EINVAL;
-    GUARD_BEGIN
-    auto *e = h->e.get();
-    const size_t need = sizeof(rve_scalars) + sizeof(size_t) + e->curve.size() * sizeof(rve_step_result) + e->state_bytes();
-    if (!buf) { *len = need; return RVE_OK; }
-    if (*len < need) return RVE_EINVAL;
-    char *p = (char *)buf;
-    std::memcpy(p, &e->S, sizeof(rve_scalars)); p += sizeof(rve_scalars);
-    size_t nc = e->curve.size();
-    std::memcpy(p, &nc, sizeof(size_t)); p += sizeof(size_t);
-    std::memcpy(p, e->curve.data(), nc * sizeof(rve_step_result)); p += nc * sizeof(rve_step_result);
-    e->save_state(p);
-    *len = need;
-    return RVE_OK;
-    GUARD_END
-}
-
-int rve_load(rve_handle h, const void *buf, size_t len) {
-    if (!h || !buf) return RVE_EINVAL;
-    GUARD_BEGIN
-    auto *e = h->e.get();
-    if (!e->micro_set) return RVE_ESTATE;
-    const char *p = (const char *)buf;
-    if (len < sizeof(rve_scalars) + sizeof(size_t)) return RVE_EINVAL;
-    rve_scalars s;
-    std::memcpy(&s, p, sizeof(s)); p += sizeof(s);
-    size_t nc;
-    std::memcpy(&nc, p, sizeof(size_t)); p += sizeof(size_t);
-    const size_t need = sizeof(rve_scalars) + sizeof(size_t) + nc * sizeof(rve_step_result) + e->state_bytes();
-    if (len != need) return RVE_EINVAL;
-    std::vector<rve_step_result> cv(nc);
-    std::memcpy(cv.data(), p, nc * sizeof(rve_step_result)); p += nc * sizeof(rve_step_result);
-    e->load_state(p);
-    e->S = s;
-    e->curve = cv;
-    return RVE_OK;
-    GUARD_END
-}
-
-int rve_timing_enable(rve_handle h, int on) {
-    if (!h) return RVE_EINVAL;
-    h->e->timing = on != 0;
-    h->e->timing_reset();
-    return RVE_OK;
-}
-
-int rve_timing_get(rve_handle h, int kind, double *total_ms, long *launches, double *bytes_per_launch) {
-    if (!h || (kind != 0 && kind != 1)) return RVE_EINVAL;
-    GUARD_BEGIN
-    double ms = 0.0, b = 0.0;
-    long n = 0;
-    h->e->timing_get(kind, ms, n, b);
-    if (total_ms) *total_ms = ms;
-    if (launches) *launches = n;
-    if (bytes_per_launch) *bytes_per_launch = b;
-    return RVE_OK;
-    GUARD_END
-}
-
-long rve_launch_count(rve_handle h) { return h ? h->e->launches : 0; }
-
-int rve_tile_config(rve_handle h, int *cw_y, int *cw_z) {
-    if (!h || !cw_y || !cw_z) return RVE_EINVAL;
-    *cw_y = h->e->cw_y;
-    *cw_z = h->e->g.nz >= 4 ? h->e->cw_z : 0;
-    return RVE_OK;
-}
-
-int rve_destroy(rve_handle h) {
-    if (!h) return RVE_EINVAL;
-    delete h;
-    return RVE_OK;
-}
-
-const char *rve_strerror(int s) {
-    switch (s) {
-    case RVE_OK: return "ok";
-    case RVE_EINVAL: return "invalid argument";
-    case RVE_ENOMEM: return "device allocation failed";
-    case RVE_ESTATE: return "call out of order";
-    case RVE_ENOCONV: return g_last_error.empty() ? "iteration did not converge" : g_last_error.c_str();
-    case RVE_ENOROOT: return g_last_error.empty() ? "dissipation constraint could not be bracketed" : g_last_error.c_str();
-    case RVE_ETIMEOUT: return "device wait timed out";
-    case RVE_ENOTFRACTURED: return "fracture point not reached";
-    case RVE_ECUDA: return g_last_error.empty() ? "CUDA error" : g_last_error.c_str();
-    case RVE_EBREAKDOWN: return g_last_error.empty() ? "CG breakdown or non-finite value" : g_last_error.c_str();
-    default: return "unknown status";
-    }
-}
-
-}  // extern "C"

@@ -5,9 +5,18 @@
 // is a symmetric NS x NS matrix per grain. Field arrays are component-major [c][voxel].
 #pragma once
 
+#include <type_traits>
+
 #include "pff_common.cuh"
 
 namespace pff {
+
+// Field words per voxel that a fused prologue / epilogue / pointwise functor reads plus writes: its
+// algorithmic memory traffic in words of the field precision (the int32 grain id counts as one,
+// per-grain tables are not counted). Functors state it as RW; 0 when they do not.
+template <class F, class = void> struct rw_words_of { static constexpr int v = 0; };
+template <class F> struct rw_words_of<F, std::void_t<decltype(F::RW)>> { static constexpr int v = F::RW; };
+template <class F> constexpr int rw_words() { return rw_words_of<F>::v; }
 
 template <typename T> __device__ __forceinline__ T degr(T phi, T k) {
     T a = (T)1 - phi;
@@ -40,6 +49,7 @@ struct MechBase {
 template <typename T, int NS>
 struct ProStressTotal : MechBase<T, NS> {
     static constexpr int NR = 1;
+    static constexpr int RW = NS + 2;  // x; phi, gid
     const T *x;
     T f[NS];
     __device__ void eval(long long v, T *out, double *acc) const {
@@ -205,9 +215,6 @@ struct XiTab {
     }
 };
 
-template <typename C> struct real_of;
-template <> struct real_of<double2> { typedef double type; };
-template <> struct real_of<float2> { typedef float type; };
 
 __device__ __forceinline__ double inv_sqrt(double v) { return 1.0 / sqrt(v); }
 __device__ __forceinline__ float inv_sqrt(float v) { return rsqrtf(v); }
@@ -275,6 +282,7 @@ struct OpProj {
 template <typename T, int NS>
 struct EpiMechInit {
     static constexpr int NR = 1;
+    static constexpr int RW = NS;  // r
     bool skip_if_done;
     T *r;
     long long N;
@@ -368,6 +376,7 @@ struct PwMechUpdate {
 template <typename T, int NS>
 struct ProCGCG : MechBase<T, NS> {
     static constexpr int NR = 0;
+    static constexpr int RW = 9 * NS + 2;  // r, p, w, s, x read; p, s, x, r written; phi, gid
     T *x, *r, *p, *s;
     const T *w;
     const Scal *scr;
@@ -395,6 +404,7 @@ struct ProCGCG : MechBase<T, NS> {
 template <typename T, int NS>
 struct EpiCGCG {
     static constexpr int NR = 2;
+    static constexpr int RW = 2 * NS;  // w written, r read
     bool skip_if_done;
     T *w;
     const T *r;
@@ -435,9 +445,71 @@ struct EpiCGCG {
             sc->alpha = gamma / den;
             sc->beta = beta;
             sc->rz = gamma;
-            if (gamma <= sc->tol2 * sc->scale2 || sc->iters >= sc->max_iters) sc->done = 1;
+            if (gamma <= sc->tol2 * sc->scale2 || gamma <= sc->eta2 * sc->rr0 || sc->iters >= sc->max_iters)
+                sc->done = 1;
         }
     };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+// ---- FP64 residual of the FP32 path (mixed-precision iterative refinement) ----------------------
+// The solution x is kept in FP64; each refinement pass evaluates the true equilibrium residual
+// r = -P[g(phi) C : (f + x)] in FP64 (FP64 transforms, FP64 stiffness table), stores it in FP32 as
+// the start of a CG on the correction, and the correction is added to x in FP64 afterwards.
+template <int NS>
+struct ProStressTotal64 {
+    static constexpr int NR = 1;
+    static constexpr int RW = 2 * NS + 2;  // x (double: two words), phi, gid
+    bool skip_if_done;
+    const double *Cm;   // [grain][NS][NS], FP64
+    const int *gid;
+    const float *phi;
+    double k;
+    const double *x;
+    double f[NS];
+    long long N;
+    __device__ void eval(long long v, double *out, double *acc) const {
+        const double *C = Cm + (size_t)ldro(gid + v) * NS * NS;
+        const double gp = degr((double)ldro(phi + v), k);
+        double u[NS];
+#pragma unroll
+        for (int a = 0; a < NS; ++a) u[a] = f[a] + ldro(x + a * N + v);
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+            double su = 0.0, sf = 0.0;
+#pragma unroll
+            for (int b = 0; b < NS; ++b) {
+                su += C[a * NS + b] * u[b];
+                sf += C[a * NS + b] * f[b];
+            }
+            out[a] = gp * su;
+            acc[0] += gp * sf * gp * sf;
+        }
+    }
+    struct Fin {
+        Scal *sc;
+        __device__ void operator()(const double *t) const { sc->scale2 = t[0]; }
+    };
+    __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
+};
+
+// r = -P[s] from the FP64 pass, stored in FP32; reduces <r, r> in FP64 and starts the CG (as
+// EpiMechInit).
+template <int NS>
+struct EpiMechInit64 {
+    static constexpr int NR = 1;
+    static constexpr int RW = NS;
+    bool skip_if_done;
+    float *r;
+    long long N;
+    __device__ void apply(long long v, const double *val, double *acc) const {
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+            r[a * N + v] = (float)(-val[a]);
+            acc[0] += val[a] * val[a];
+        }
+    }
+    typedef typename EpiMechInit<double, NS>::Fin Fin;
     __device__ Fin fin(Scal *sc) const { return Fin{sc}; }
 };
 
@@ -445,6 +517,7 @@ struct EpiCGCG {
 template <typename T, int NS>
 struct PwPsi1 {
     static constexpr int NR = 0;
+    static constexpr int RW = NS + 2;  // x, gid; psi1
     static constexpr bool MAXRED = false;
     bool skip_if_done;
     const T *Cm, *x;
@@ -493,6 +566,7 @@ struct DmgCoef {
 template <typename T>
 struct ProDmgInit {
     static constexpr int NR = 2;
+    static constexpr int RW = 5;  // psi1, psi_ini, H^n, x read; H_E written
     bool skip_if_done;
     int mode;            // 0: damage with history, 1: damage without history, 2: fixed rhs field
     double E;
@@ -535,6 +609,7 @@ struct ProDmgInit {
 template <typename T>
 struct PwDmgInitKept {
     static constexpr int NR = 4;
+    static constexpr int RW = 8;  // psi1, psi_ini, H^n, x, div, gid; H_E, r
     static constexpr bool MAXRED = false;
     bool skip_if_done;
     int mode;  // 0: with history, 1: without
@@ -581,6 +656,7 @@ struct PwDmgInitKept {
 template <typename T>
 struct ProField {
     static constexpr int NR = 0;
+    static constexpr int RW = 1;
     bool skip_if_done;
     const T *f;
     __device__ void eval(long long v, T *out, double *) const { out[0] = f[v]; }
@@ -649,6 +725,7 @@ struct OpPrec {  // v^ / (abar + bbar |xi~|^2)
 template <typename T>
 struct ProPCGCG {
     static constexpr int NR = 0;
+    static constexpr int RW = 10;  // u, p, w, s, r, x read; p, s, x, r written
     bool skip_if_done;
     T *x, *r, *p, *s;
     const T *u, *w;
@@ -692,6 +769,7 @@ struct OpPrecGrad {  // r^ -> [u^ = r^ / (abar + bbar |xi~|^2), i xi~_a u^]
 
 template <typename T, int D>
 struct MidFluxU {  // [u, grad u] -> store u, K grad u
+    static constexpr int RW = 2;  // gid; u written
     bool skip_if_done;
     const T *Ktab;
     const int *gid;
@@ -715,6 +793,7 @@ template <typename T> struct DmgCoef;
 template <typename T>
 struct EpiPCGCG {
     static constexpr int NR = 3;
+    static constexpr int RW = 5;  // gid, H, u, r read; w written
     bool skip_if_done;
     const T *acoef;
     const int *gid;
@@ -766,6 +845,7 @@ struct EpiPCGCG {
 
 template <typename T, int D>
 struct MidFlux {  // grad v -> K grad v
+    static constexpr int RW = 1;  // gid
     bool skip_if_done;
     const T *Ktab;
     const int *gid;
@@ -789,6 +869,7 @@ struct MidFlux {  // grad v -> K grad v
 template <typename T>
 struct EpiDmgRes {
     static constexpr int NR = 2;
+    static constexpr int RW = 6;  // x, gid, H, rhs; r, div
     bool skip_if_done;
     DmgCoef<T> co;
     const T *x;
@@ -825,6 +906,7 @@ struct EpiDmgRes {
 template <typename T>
 struct PwDmgEnergy {
     static constexpr int NR = 1;
+    static constexpr int RW = 5;  // x, r, rhs, H, gid
     static constexpr bool MAXRED = false;
     bool skip_if_done;
     DmgCoef<T> co;
@@ -848,6 +930,7 @@ struct PwDmgEnergy {
 template <typename T>
 struct EpiApply {
     static constexpr int NR = 0;
+    static constexpr int RW = 4;  // v, gid, H; out
     bool skip_if_done;
     DmgCoef<T> co;
     const T *v_in;
@@ -861,6 +944,7 @@ struct EpiApply {
 template <typename T>
 struct EpiStore {
     static constexpr int NR = 0;
+    static constexpr int RW = 1;
     bool skip_if_done;
     T *out;
     __device__ void apply(long long v, const T *val, double *) const { out[v] = val[0]; }
@@ -873,6 +957,7 @@ struct EpiStore {
 template <typename T, int D>
 struct EpiDiss {
     static constexpr int NR = 2;
+    static constexpr int RW = 2;  // phi, gid
     bool skip_if_done;
     const T *phi;
     const T *GcTab, *Atab;

@@ -4,9 +4,9 @@
 //   k_x_fwd   : per pair of x-rows, evaluate the prologue (e.g. the stress C_phi : p of a CG
 //               direction) for NC components, pack the two real rows as one complex line, FFT
 //               along x in shared memory, split into the two half spectra, store [c][z][y][kx];
-//   k_axis    : per tile of CW adjacent kx columns, FFT along y (2D) or y then z (3D) in shared
-//               memory, apply the per-frequency operator (projection, gradient, divergence,
-//               preconditioner), inverse FFT, store;
+//   k_axis    : per tile of CW adjacent kx columns, FFT along y (2D) or y then z (3D), one warp
+//               per line in registers, apply the per-frequency operator (projection, gradient,
+//               divergence, preconditioner), inverse FFT, store;
 //   k_x_inv   : rebuild the packed line from two half spectra, inverse FFT along x, evaluate the
 //               epilogue (CG vector update, residual, dot products) with a deterministic
 //               reduction finalised by the last CTA.
@@ -23,9 +23,9 @@ enum { AX_FWD = 0, AX_INV = 1, AX_FWD_OP_INV = 2 };
 
 // ---- x-axis forward (r2c) pass ------------------------------------------------------------------
 template <typename T, int NC, class Pro>
-__global__ void __launch_bounds__(512) k_x_fwd(Geom g, Pro pro, typename cplx_of<T>::type *__restrict__ spec,
-                                               const typename cplx_of<T>::type *__restrict__ tw, double *partials,
-                                               Scal *sc) {
+__device__ __forceinline__ void x_fwd_body(const Geom &g, const Pro &pro, typename cplx_of<T>::type *__restrict__ spec,
+                                           const typename cplx_of<T>::type *__restrict__ tw, double *partials,
+                                           Scal *sc) {
     typedef typename cplx_of<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *s = reinterpret_cast<C *>(smem_raw);
@@ -71,6 +71,35 @@ __global__ void __launch_bounds__(512) k_x_fwd(Geom g, Pro pro, typename cplx_of
     if constexpr (Pro::NR > 0) reduce_finalize<Pro::NR>(acc, partials, sc, pro.fin(sc));
 }
 
+template <typename T, int NC, class Pro>
+__global__ void __launch_bounds__(512) k_x_fwd(Geom g, Pro pro, typename cplx_of<T>::type *__restrict__ spec,
+                                               const typename cplx_of<T>::type *__restrict__ tw, double *partials,
+                                               Scal *sc) {
+    x_fwd_body<T, NC>(g, pro, spec, tw, partials, sc);
+}
+
+// ---- batched launches: several RVEs of one grid in one launch -----------------------------------
+// blockIdx.z selects the RVE; each carries its own functor, spectral buffer, reduction partials
+// and scalar block (the per-RVE reductions see gridDim.x * gridDim.y blocks, as unbatched).
+constexpr int kMaxBatch = 16;
+template <class F> struct SlotArg {
+    F f;
+    void *spec;
+    double *partials;
+    Scal *sc;
+};
+template <class F> struct SlotArgs {
+    SlotArg<F> a[kMaxBatch];
+};
+
+template <typename T, int NC, class Pro>
+__global__ void __launch_bounds__(512) k_x_fwd_b(Geom g, SlotArgs<Pro> args,
+                                                 const typename cplx_of<T>::type *__restrict__ tw) {
+    typedef typename cplx_of<T>::type C;
+    const SlotArg<Pro> &a = args.a[blockIdx.z];
+    x_fwd_body<T, NC>(g, a.f, (C *)a.spec, tw, a.partials, a.sc);
+}
+
 // Load the packed complex line Z = Xa + i Xb of rows (y0, y0+1) from the half spectra.
 template <typename T, typename C>
 __device__ __forceinline__ void load_packed(const Geom &g, const C *__restrict__ spec, int c, int z, int y0,
@@ -100,9 +129,9 @@ __device__ __forceinline__ void load_packed(const Geom &g, const C *__restrict__
 
 // ---- x-axis inverse (c2r) pass with a fused epilogue --------------------------------------------
 template <typename T, int NC, class Epi>
-__global__ void __launch_bounds__(512) k_x_inv(Geom g, const typename cplx_of<T>::type *__restrict__ spec, Epi epi,
-                                               const typename cplx_of<T>::type *__restrict__ tw, double *partials,
-                                               Scal *sc) {
+__device__ __forceinline__ void x_inv_body(const Geom &g, const typename cplx_of<T>::type *__restrict__ spec,
+                                           const Epi &epi, const typename cplx_of<T>::type *__restrict__ tw,
+                                           double *partials, Scal *sc) {
     typedef typename cplx_of<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *s = reinterpret_cast<C *>(smem_raw);
@@ -139,12 +168,27 @@ __global__ void __launch_bounds__(512) k_x_inv(Geom g, const typename cplx_of<T>
     if constexpr (Epi::NR > 0) reduce_finalize<Epi::NR>(acc, partials, sc, epi.fin(sc));
 }
 
+template <typename T, int NC, class Epi>
+__global__ void __launch_bounds__(512) k_x_inv(Geom g, const typename cplx_of<T>::type *__restrict__ spec, Epi epi,
+                                               const typename cplx_of<T>::type *__restrict__ tw, double *partials,
+                                               Scal *sc) {
+    x_inv_body<T, NC>(g, spec, epi, tw, partials, sc);
+}
+
+template <typename T, int NC, class Epi>
+__global__ void __launch_bounds__(512) k_x_inv_b(Geom g, SlotArgs<Epi> args,
+                                                 const typename cplx_of<T>::type *__restrict__ tw) {
+    typedef typename cplx_of<T>::type C;
+    const SlotArg<Epi> &a = args.a[blockIdx.z];
+    x_inv_body<T, NC>(g, (const C *)a.spec, a.f, tw, a.partials, a.sc);
+}
+
 // ---- x-axis inverse, pointwise map, x-axis forward ----------------------------------------------
 // Inverse x pass of NCI components, mid.apply(v, in[NCI], out[NCO]) per voxel (NCO <= NCI), forward
 // x pass of the NCO outputs.
 template <typename T, int NCI, int NCO, class Mid>
-__global__ void __launch_bounds__(512) k_x_mid(Geom g, typename cplx_of<T>::type *__restrict__ spec, Mid mid,
-                                               const typename cplx_of<T>::type *__restrict__ tw, Scal *sc) {
+__device__ __forceinline__ void x_mid_body(const Geom &g, typename cplx_of<T>::type *__restrict__ spec, const Mid &mid,
+                                           const typename cplx_of<T>::type *__restrict__ tw, Scal *sc) {
     typedef typename cplx_of<T>::type C;
     static_assert(NCO <= NCI, "k_x_mid maps NCI components to at most NCI");
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -198,75 +242,358 @@ __global__ void __launch_bounds__(512) k_x_mid(Geom g, typename cplx_of<T>::type
     }
 }
 
-// ---- y / z axis pass ------------------------------------------------------------------------------
-// axis = 1 (y) or 2 (z). A CTA owns CW adjacent kx columns of one plane (z for axis y, y for
-// axis z) and all L points along the axis. MODE: AX_FWD, AX_INV or AX_FWD_OP_INV (forward, the
-// per-frequency operator mapping NCI -> NCO components, inverse).
-template <typename T, int NCI, int NCO, int MODE, class Op>
-__global__ void __launch_bounds__(512) k_axis(Geom g, int axis, const typename cplx_of<T>::type *spec_in,
-                                              typename cplx_of<T>::type *spec_out, Op op,
-                                              const typename cplx_of<T>::type *__restrict__ tw, Scal *sc) {
+template <typename T, int NCI, int NCO, class Mid>
+__global__ void __launch_bounds__(512) k_x_mid(Geom g, typename cplx_of<T>::type *__restrict__ spec, Mid mid,
+                                               const typename cplx_of<T>::type *__restrict__ tw, Scal *sc) {
+    x_mid_body<T, NCI, NCO>(g, spec, mid, tw, sc);
+}
+
+template <typename T, int NCI, int NCO, class Mid>
+__global__ void __launch_bounds__(512) k_x_mid_b(Geom g, SlotArgs<Mid> args,
+                                                 const typename cplx_of<T>::type *__restrict__ tw) {
     typedef typename cplx_of<T>::type C;
-    constexpr int NM = NCI > NCO ? NCI : NCO;
+    const SlotArg<Mid> &a = args.a[blockIdx.z];
+    x_mid_body<T, NCI, NCO>(g, (C *)a.spec, a.f, tw, a.sc);
+}
+
+
+// ---- y / z axis pass ----------------------------------------------------------------------------
+// axis = 1 (y) or 2 (z). A CTA owns CW adjacent kx columns of one plane (z for axis y, y for
+// axis z) and all L points along the axis, for every component. MODE: AX_FWD, AX_INV or
+// AX_FWD_OP_INV (forward, the per-frequency operator mapping NCI -> NCO components, inverse).
+//
+//  1. The tile is read from global memory with consecutive threads on consecutive kx (coalesced
+//     runs of CW complex values per row) into shared memory, one line of L points per
+//     (component, column). Lines are padded so that the transposing writes hit distinct banks.
+//  2. Each line is transformed by one warp (or a lane group of S = L / R lanes when L < 128) in
+//     registers: lane l holds the R points l + S m (m < R); an R-point decimation-in-frequency
+//     FFT over m, a twiddle by w_L^(l k1), then an S-point DIF across the lanes with shuffles
+//     (see wfft_fwd). No CTA barrier is taken inside a transform. The spectrum is left in the
+//     scrambled storage order of the network: position p = l + S m holds the frequency
+//     axis_freq(p) = brev_R(m) + R brev_S(l); the operator is evaluated there, and the inverse
+//     network (wfft_inv) takes that order back to natural order. In 3D the y pass stores its
+//     spectrum in storage order between the forward and the inverse y passes, so the z pass
+//     maps its plane index through axis_freq as well.
+template <int R> struct log2_of { static constexpr int v = R == 1 ? 0 : 1 + log2_of<R / 2>::v; };
+template <> struct log2_of<1> { static constexpr int v = 0; };
+
+// Points per lane of the warp transform of a line of L points (S = L / R lanes, S <= 32).
+__host__ __device__ constexpr int axis_points_per_lane(int L) {
+    return L <= 128 ? 4 : (L == 256 ? 8 : (L == 512 ? 16 : 32));
+}
+__device__ __forceinline__ int brev_bits(int v, int bits) {
+    return bits == 0 ? 0 : (int)(__brev((unsigned)v) >> (32 - bits));
+}
+__device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
+// Frequency index held at storage position p of a line of L points after wfft_fwd.
+__device__ __forceinline__ int axis_freq(int p, int L) {
+    const int R = axis_points_per_lane(L);
+    const int lgR = ilog2(R), lgS = ilog2(L) - lgR;
+    const int m = p >> lgS, l = p & ((1 << lgS) - 1);
+    return brev_bits(m, lgR) + (brev_bits(l, lgS) << lgR);
+}
+
+__device__ __forceinline__ double2 shfl_xor_c(double2 v, int m) {
+    return make_double2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+__device__ __forceinline__ float2 shfl_xor_c(float2 v, int m) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+template <typename C> __device__ __forceinline__ C conj_c(C a) { a.y = -a.y; return a; }
+
+// w_32^t = exp(-2 pi i t / 32), t < 32: the twiddles of the in-register stages (R <= 32), at
+// offsets known at compile time, so they are read from the constant bank. Each translation unit
+// that includes this header has its own copy; axis_twiddles_init() fills it on the current device.
+static __constant__ double2 c_w32d[32];
+static __constant__ float2 c_w32f[32];
+template <typename C> __device__ __forceinline__ C w32(int t);
+template <> __device__ __forceinline__ double2 w32<double2>(int t) { return c_w32d[t]; }
+template <> __device__ __forceinline__ float2 w32<float2>(int t) { return c_w32f[t]; }
+
+static inline cudaError_t axis_twiddles_init() {
+    double2 d[32];
+    float2 f[32];
+    for (int t = 0; t < 32; ++t) {
+        const long double a = -2.0L * 3.14159265358979323846264338327950288L * (long double)t / 32.0L;
+        d[t] = make_double2((double)cosl(a), (double)sinl(a));
+        f[t] = make_float2((float)cosl(a), (float)sinl(a));
+    }
+    cudaError_t e = cudaMemcpyToSymbol(c_w32d, d, sizeof(d));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w32f, f, sizeof(f));
+    return e;
+}
+
+// Forward transform of one line: v[m] = x[l + S m] on entry, v[m] = X[axis_freq(l + S m)] on
+// exit (unnormalised, w_L = exp(-2 pi i / L), tw[j] = w_L^j). Every lane of the warp must call it.
+template <typename C, int R>
+__device__ __forceinline__ void wfft_fwd(C (&v)[R], int l, int S, int L, const C *__restrict__ tw) {
+    constexpr int lgR = log2_of<R>::v;
+#pragma unroll
+    for (int h = R / 2; h >= 1; h >>= 1) {
+#pragma unroll
+        for (int b = 0; b < R; b += 2 * h) {
+#pragma unroll
+            for (int j = 0; j < h; ++j) {
+                const C a = v[b + j], c = v[b + j + h];
+                v[b + j] = cadd(a, c);
+                const C d = csub(a, c);
+                v[b + j + h] = j == 0 ? d : cmul(d, w32<C>(j * (16 / h)));
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 1; m < R; ++m) {
+        const int k1 = (int)(__brev((unsigned)m) >> (32 - lgR));
+        v[m] = cmul(v[m], tw[(l * k1) & (L - 1)]);
+    }
+    // lane stage h: the lower lane of a pair keeps a + b, the upper one (a - b) w. Both are
+    // t w~ with t = o + sgn v (sgn = -1 on the upper lane) and w~ = 1 on the lower lane, so every
+    // lane runs the same instructions (no divergent halves).
+    for (int h = S >> 1; h >= 1; h >>= 1) {
+        const bool upper = (l & h) != 0;
+        typedef typename real_of<C>::type Rt;
+        const Rt sg = upper ? (Rt)-1 : (Rt)1;
+        C w = tw[(l & (h - 1)) * (L / (2 * h))];
+        if (!upper) { w.x = (Rt)1; w.y = (Rt)0; }
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            const C o = shfl_xor_c(v[m], h);
+            C t;
+            t.x = fma(sg, v[m].x, o.x);
+            t.y = fma(sg, v[m].y, o.y);
+            v[m] = cmul(t, w);
+        }
+    }
+}
+
+// Inverse of wfft_fwd up to the factor L: storage order in, natural order out (unnormalised
+// inverse DFT). Every lane of the warp must call it.
+template <typename C, int R>
+__device__ __forceinline__ void wfft_inv(C (&v)[R], int l, int S, int L, const C *__restrict__ tw) {
+    constexpr int lgR = log2_of<R>::v;
+    // inverse lane stage h: the upper lane sends u = conj(w) b', the lower one a'; the lower lane
+    // keeps a' + u, the upper one a' - u, i.e. o + sgn send with sgn = -1 on the upper lane.
+    for (int h = 1; h < S; h <<= 1) {
+        const bool upper = (l & h) != 0;
+        typedef typename real_of<C>::type Rt;
+        const Rt sg = upper ? (Rt)-1 : (Rt)1;
+        C w = conj_c(tw[(l & (h - 1)) * (L / (2 * h))]);
+        if (!upper) { w.x = (Rt)1; w.y = (Rt)0; }
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            const C send = cmul(v[m], w);
+            const C o = shfl_xor_c(send, h);
+            v[m].x = fma(sg, send.x, o.x);
+            v[m].y = fma(sg, send.y, o.y);
+        }
+    }
+#pragma unroll
+    for (int m = 1; m < R; ++m) {
+        const int k1 = (int)(__brev((unsigned)m) >> (32 - lgR));
+        v[m] = cmul(v[m], conj_c(tw[(l * k1) & (L - 1)]));
+    }
+#pragma unroll
+    for (int h = 1; h < R; h <<= 1) {
+#pragma unroll
+        for (int b = 0; b < R; b += 2 * h) {
+#pragma unroll
+            for (int j = 0; j < h; ++j) {
+                const C t = j == 0 ? v[b + j + h] : cmul(v[b + j + h], conj_c(w32<C>(j * (16 / h))));
+                const C a = v[b + j];
+                v[b + j] = cadd(a, t);
+                v[b + j + h] = csub(a, t);
+            }
+        }
+    }
+}
+
+// Padding of a shared-memory line (complex elements): with CW columns read per row, the rows of
+// one 128-byte phase of a warp access land on distinct banks.
+template <typename C> __host__ __device__ constexpr int axis_line_pad(int CW) {
+    return (int)(128 / sizeof(C)) / CW;
+}
+
+// Transform the lines [0, nlines) of the tile, one line per lane group of S lanes, looping over
+// groups of lines when there are more lines than warps. INV selects the inverse network.
+template <typename C, int R, bool INV>
+__device__ __forceinline__ void axis_lines(C *s, int nlines, int LS, int L, const C *__restrict__ tw) {
+    const int S = L / R;
+    const int lpw = 32 / S;  // lines per warp
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int l = lane & (S - 1);
+    for (int grp = warp; grp * lpw < nlines; grp += nwarps) {  // uniform across the warp
+        const int line = grp * lpw + lane / S;
+        const bool valid = line < nlines;
+        C *p = s + (size_t)(valid ? line : 0) * LS;
+        C v[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = p[l + S * m];
+        if constexpr (INV) wfft_inv<C, R>(v, l, S, L, tw);
+        else wfft_fwd<C, R>(v, l, S, L, tw);
+        __syncwarp();
+        if (valid) {
+#pragma unroll
+            for (int m = 0; m < R; ++m) p[l + S * m] = v[m];
+        }
+        __syncwarp();
+    }
+}
+
+// Threads per CTA at most: 512, or 256 where a lane holds 16 or more values (more registers each).
+template <typename T> __host__ __device__ constexpr int axis_max_threads(int R) {
+    return (R >= 16 || (sizeof(T) == 8 && R >= 8)) ? 256 : 512;
+}
+
+template <typename T, int NCI, int NCO, int MODE, int R, class Op>
+__device__ __forceinline__ void axis_body(const Geom &g, int axis, int CW,
+                                          const typename cplx_of<T>::type *__restrict__ spec_in,
+                                          typename cplx_of<T>::type *spec_out, const Op &op,
+                                          const typename cplx_of<T>::type *__restrict__ tw, Scal *sc) {
+    typedef typename cplx_of<T>::type C;
     constexpr int NOUT = (MODE == AX_FWD_OP_INV) ? NCO : NCI;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *s = reinterpret_cast<C *>(smem_raw);
     if (op.skip_if_done && sc->done) return;
     const int L = axis == 1 ? g.ny : g.nz;
-    const int logL = axis == 1 ? g.ly : g.lz;
-    const int TL = L >> 2;
-    const int CW = blockDim.x / TL;
+    const int lgL = axis == 1 ? g.ly : g.lz;
+    const int lgCW = ilog2(CW);
+    const int LS = L + axis_line_pad<C>(CW);
     const int kx0 = blockIdx.x * CW;
     const int other = blockIdx.y;
     const long long lstride = axis == 1 ? (long long)g.Px : (long long)g.Px * g.ny;
     const long long base = axis == 1 ? (long long)other * g.ny * g.Px : (long long)other * g.Px;
-    // blockDim.x = CW * L / 4: every loop over the tile's L * CW points takes exactly 4 steps,
-    // unrolled (fully up to 4 components, by 2 beyond, to stay within the register budget)
-    constexpr int UQ = NM <= 4 ? 4 : 2;
-    const int nthreads = blockDim.x;
-#pragma unroll UQ
-    for (int q = 0; q < 4; ++q) {
-        const int i = threadIdx.x + q * nthreads;
-        const int pos = i / CW, cc = i - pos * CW;
+    const int nth = blockDim.x;
+    const int npt = L * CW;  // points of one component in the tile
+    // 1. coalesced load: i = (c, pos, cc), cc fastest. Each thread issues UB loads before it
+    //    stores any of them, so that many loads are in flight. The tile belongs to this CTA alone
+    //    and is read before any of it is written back, so the read-only path is safe in place.
+    //    (Asynchronous 8-byte copies straight to shared memory measured 1.3-2x slower.)
+    constexpr int UB = 8;
+    for (int i0 = threadIdx.x; i0 < NCI * npt; i0 += nth * UB) {
+        C tmp[UB];
 #pragma unroll
-        for (int c = 0; c < NCI; ++c)
-            s[(size_t)(c * CW + cc) * L + pos] = spec_in[(size_t)c * g.Nh + base + pos * lstride + kx0 + cc];
+        for (int u = 0; u < UB; ++u) {
+            const int i = i0 + u * nth;
+            if (i < NCI * npt) {
+                const int c = i >> (lgL + lgCW);
+                const int rem = i & (npt - 1);
+                const int pos = rem >> lgCW, cc = rem & (CW - 1);
+                tmp[u] = __ldg(spec_in + (size_t)c * g.Nh + base + pos * lstride + kx0 + cc);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int i = i0 + u * nth;
+            if (i < NCI * npt) {
+                const int c = i >> (lgL + lgCW);
+                const int rem = i & (npt - 1);
+                const int pos = rem >> lgCW, cc = rem & (CW - 1);
+                s[(size_t)((c << lgCW) + cc) * LS + pos] = tmp[u];
+            }
+        }
     }
     __syncthreads();
-    if constexpr (MODE == AX_INV) {
-        fft_lines<C, NM>(s, L, logL, NCI, 1, CW, tw, true);
-    } else {
-        fft_lines<C, NM>(s, L, logL, NCI, 1, CW, tw, false);
-    }
+    // 2. transforms (and the operator between them)
+    axis_lines<C, R, MODE == AX_INV>(s, NCI * CW, LS, L, tw);
     if constexpr (MODE == AX_FWD_OP_INV) {
-#pragma unroll UQ
-        for (int q = 0; q < 4; ++q) {
-            const int i = threadIdx.x + q * nthreads;
-            const int pos = i / CW, cc = i - pos * CW;
+        __syncthreads();
+        for (int i = threadIdx.x; i < npt; i += nth) {
+            const int cc = i >> lgL, p = i & (L - 1);
+            const int kk = axis_freq(p, L);
             const int kx = kx0 + cc;
-            const int ky = axis == 1 ? pos : other;
-            const int kz = axis == 1 ? (g.nz > 1 ? other : 0) : pos;
+            const int ky = axis == 1 ? kk : axis_freq(other, g.ny);
+            const int kz = axis == 1 ? (g.nz > 1 ? other : 0) : kk;
             C in[NCI], out[NCO];
 #pragma unroll
-            for (int c = 0; c < NCI; ++c) in[c] = s[(size_t)(c * CW + cc) * L + pos];
+            for (int c = 0; c < NCI; ++c) in[c] = s[(size_t)((c << lgCW) + cc) * LS + p];
             op.apply(g, kx, ky, kz, in, out);
 #pragma unroll
-            for (int c = 0; c < NCO; ++c) s[(size_t)(c * CW + cc) * L + pos] = out[c];
+            for (int c = 0; c < NCO; ++c) s[(size_t)((c << lgCW) + cc) * LS + p] = out[c];
         }
         __syncthreads();
-        fft_lines<C, NM>(s, L, logL, NCO, 1, CW, tw, true);
+        axis_lines<C, R, true>(s, NCO * CW, LS, L, tw);
     }
-#pragma unroll UQ
-    for (int q = 0; q < 4; ++q) {
-        const int i = threadIdx.x + q * nthreads;
-        const int pos = i / CW, cc = i - pos * CW;
-#pragma unroll
-        for (int c = 0; c < NOUT; ++c)
-            spec_out[(size_t)c * g.Nh + base + pos * lstride + kx0 + cc] = s[(size_t)(c * CW + cc) * L + pos];
+    __syncthreads();
+    // 3. coalesced store
+    for (int i = threadIdx.x; i < NOUT * npt; i += nth) {
+        const int c = i >> (lgL + lgCW);
+        const int rem = i & (npt - 1);
+        const int pos = rem >> lgCW, cc = rem & (CW - 1);
+        spec_out[(size_t)c * g.Nh + base + pos * lstride + kx0 + cc] = s[(size_t)((c << lgCW) + cc) * LS + pos];
+    }
+}
+
+template <typename T, int NCI, int NCO, int MODE, int R, class Op>
+__global__ void __launch_bounds__(axis_max_threads<T>(R))
+    k_axis(Geom g, int axis, int CW, const typename cplx_of<T>::type *__restrict__ spec_in,
+           typename cplx_of<T>::type *spec_out, Op op, const typename cplx_of<T>::type *__restrict__ tw, Scal *sc) {
+    axis_body<T, NCI, NCO, MODE, R>(g, axis, CW, spec_in, spec_out, op, tw, sc);
+}
+
+template <typename T, int NCI, int NCO, int MODE, int R, class Op>
+__global__ void __launch_bounds__(axis_max_threads<T>(R))
+    k_axis_b(Geom g, int axis, int CW, SlotArgs<Op> args, const typename cplx_of<T>::type *__restrict__ tw) {
+    typedef typename cplx_of<T>::type C;
+    const SlotArg<Op> &a = args.a[blockIdx.z];
+    axis_body<T, NCI, NCO, MODE, R>(g, axis, CW, (const C *)a.spec, (C *)a.spec, a.f, tw, a.sc);
+}
+
+
+// Launch shape of k_axis for an axis of L points, NM components and CW columns per CTA: one lane
+// group of S = L / R lanes per line, at most 16 warps (the warps loop over the lines beyond), and
+// the padded lines in dynamic shared memory.
+template <typename C> inline void axis_shape(int L, int NM, int CW, int &threads, size_t &smem, int wcap = 16) {
+    const int R = axis_points_per_lane(L), S = L / R;
+    const long long lanes = (long long)NM * CW * S;
+    long long w = (lanes + 31) / 32;
+    int wmax = axis_max_threads<typename real_of<C>::type>(R) / 32;
+    if (wcap >= 1 && wcap < wmax) wmax = wcap;
+    if (w > wmax) w = wmax;
+    if (w < 1) w = 1;
+    threads = (int)(32 * w);
+    smem = (size_t)NM * CW * (size_t)(L + axis_line_pad<C>(CW)) * sizeof(C);
+}
+
+template <typename T, class Op>
+using axis_kernel_t = void (*)(Geom, int, int, const typename cplx_of<T>::type *__restrict__, typename cplx_of<T>::type *,
+                               Op, const typename cplx_of<T>::type *__restrict__, Scal *);
+
+// The instance of k_axis for the points per lane of an axis of L points.
+template <typename T, int NCI, int NCO, int MODE, class Op> inline axis_kernel_t<T, Op> axis_kernel(int L) {
+    switch (axis_points_per_lane(L)) {
+    case 4: return k_axis<T, NCI, NCO, MODE, 4, Op>;
+    case 8: return k_axis<T, NCI, NCO, MODE, 8, Op>;
+    case 16: return k_axis<T, NCI, NCO, MODE, 16, Op>;
+    default: return k_axis<T, NCI, NCO, MODE, 32, Op>;
+    }
+}
+
+template <typename T, class Op>
+using axis_kernel_b_t = void (*)(Geom, int, int, SlotArgs<Op>, const typename cplx_of<T>::type *__restrict__);
+template <typename T, int NCI, int NCO, int MODE, class Op> inline axis_kernel_b_t<T, Op> axis_kernel_b(int L) {
+    switch (axis_points_per_lane(L)) {
+    case 4: return k_axis_b<T, NCI, NCO, MODE, 4, Op>;
+    case 8: return k_axis_b<T, NCI, NCO, MODE, 8, Op>;
+    case 16: return k_axis_b<T, NCI, NCO, MODE, 16, Op>;
+    default: return k_axis_b<T, NCI, NCO, MODE, 32, Op>;
     }
 }
 
 // ---- pointwise kernel with deterministic reductions ---------------------------------------------
+template <class F>
+__global__ void __launch_bounds__(256) k_pointwise_b(long long N, SlotArgs<F> args) {
+    const SlotArg<F> &a = args.a[blockIdx.z];
+    const F &f = a.f;
+    Scal *sc = a.sc;
+    if (f.skip_if_done && sc->done) return;
+    double acc[F::NR > 0 ? F::NR : 1];
+#pragma unroll
+    for (int k = 0; k < (F::NR > 0 ? F::NR : 1); ++k) acc[k] = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N; v += stride) f.apply(v, acc);
+    if constexpr (F::NR > 0) reduce_finalize<F::NR>(acc, a.partials, sc, f.fin(sc), F::MAXRED);
+}
+
 template <class F>
 __global__ void __launch_bounds__(256) k_pointwise(long long N, F f, double *partials, Scal *sc) {
     if (f.skip_if_done && sc->done) return;

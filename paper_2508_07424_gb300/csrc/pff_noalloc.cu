@@ -170,6 +170,8 @@ extern "C" int rve_dissipation_noalloc(int dim, const int n[3], double ell, int 
         // g_scratch is not a device address, so look the address up and keep it.
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return RVE_ECUDA;
+        // the column passes read their in-register twiddles from this file's constant bank
+        if (axis_twiddles_init() != cudaSuccess) return RVE_ECUDA;
         g_scratch_addr[dev] = p;
     }
     unsigned char *base = (unsigned char *)g_scratch_addr[dev];
@@ -200,9 +202,11 @@ extern "C" int rve_dissipation_noalloc(int dim, const int n[3], double ell, int 
     auto axis_launch = [&](auto kernel, int ax, int NM, const auto &op, const double2 *tw) -> cudaError_t {
         const int L = ax == 1 ? ny : nz;
         const int CW = ax == 1 ? cwy : cwz;
-        const size_t sm = (size_t)NM * CW * L * sizeof(double2);
+        int threads;
+        size_t sm;
+        axis_shape<double2>(L, NM, CW, threads, sm);
         if (sm > 32 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        kernel<<<dim3(g.Px / CW, ax == 1 ? nz : ny), CW * (L / 4), sm, st>>>(g, ax, spec, spec, op, tw, sc);
+        kernel<<<dim3(g.Px / CW, ax == 1 ? nz : ny), threads, sm, st>>>(g, ax, CW, spec, spec, op, tw, sc);
         return cudaGetLastError();
     };
 
@@ -214,7 +218,7 @@ extern "C" int rve_dissipation_noalloc(int dim, const int n[3], double ell, int 
     }
     const int32_t *gid = grain_id;
     if (dim == 2) {
-        if (axis_launch(k_axis<double, 1, 2, AX_FWD_OP_INV, OpGrad<double2, 2>>, 1, 2, OpGrad<double2, 2>{false, xi}, twy))
+        if (axis_launch(axis_kernel<double, 1, 2, AX_FWD_OP_INV, OpGrad<double2, 2>>(ny), 1, 2, OpGrad<double2, 2>{false, xi}, twy))
             return RVE_ECUDA;
         auto k = k_x_inv<double, 2, EpiDissChecked<2>>;
         const size_t sm = smx * 2;
@@ -224,16 +228,16 @@ extern "C" int rve_dissipation_noalloc(int dim, const int n[3], double ell, int 
     } else {
         if (nz == 1) {
             // plate: xi_z = 0, so the gradient is taken in the y pass, as in 2D
-            if (axis_launch(k_axis<double, 1, 3, AX_FWD_OP_INV, OpGrad<double2, 3>>, 1, 3, OpGrad<double2, 3>{false, xi},
+            if (axis_launch(axis_kernel<double, 1, 3, AX_FWD_OP_INV, OpGrad<double2, 3>>(ny), 1, 3, OpGrad<double2, 3>{false, xi},
                             twy))
                 return RVE_ECUDA;
         } else {
-            if (axis_launch(k_axis<double, 1, 1, AX_FWD, OpGrad<double2, 3>>, 1, 1, OpGrad<double2, 3>{false, xi}, twy))
+            if (axis_launch(axis_kernel<double, 1, 1, AX_FWD, OpGrad<double2, 3>>(ny), 1, 1, OpGrad<double2, 3>{false, xi}, twy))
                 return RVE_ECUDA;
-            if (axis_launch(k_axis<double, 1, 3, AX_FWD_OP_INV, OpGrad<double2, 3>>, 2, 3, OpGrad<double2, 3>{false, xi},
+            if (axis_launch(axis_kernel<double, 1, 3, AX_FWD_OP_INV, OpGrad<double2, 3>>(nz), 2, 3, OpGrad<double2, 3>{false, xi},
                             twz))
                 return RVE_ECUDA;
-            if (axis_launch(k_axis<double, 3, 3, AX_INV, OpGrad<double2, 3>>, 1, 3, OpGrad<double2, 3>{false, xi}, twy))
+            if (axis_launch(axis_kernel<double, 3, 3, AX_INV, OpGrad<double2, 3>>(ny), 1, 3, OpGrad<double2, 3>{false, xi}, twy))
                 return RVE_ECUDA;
         }
         auto k = k_x_inv<double, 3, EpiDissChecked<3>>;

@@ -3,10 +3,13 @@
 // Each request is one RVE (configuration + microstructure, copied at submission) solved by
 // repeated dissipation increments until the fracture point or an increment cap. Worker threads
 // run admitted requests concurrently, each on its own handle and CUDA stream, so the kernels of
-// different RVEs overlap on the device. Admission is first-come first-served under two limits:
-// the number of workers (slots) and an HBM budget checked against each request's device
-// footprint (rve_footprint_bytes). A request that fails is retired with its status; the others
-// keep running. Results are collected with rve_server_wait.
+// different RVEs overlap on the device. Requests of one size class (grid and precision) step
+// through a shared lockstep group (rve_step_in_group): the solve loops of the requests of a class
+// that are in flight at the same moment run as one batched launch per pass, and requests join and
+// leave their class's group as they are admitted and retired. Admission is first-come first-served
+// under two limits: the number of workers (slots) and an HBM budget checked against each request's
+// device footprint (rve_footprint_bytes). A request that fails is retired with its status; the
+// others keep running. Results are collected with rve_server_wait.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -15,8 +18,10 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
+#include <tuple>
 #include <thread>
 #include <vector>
 
@@ -50,6 +55,20 @@ struct Server {
     long submitted = 0, finished = 0;
     bool stop = false;
     int device = 0;
+    bool batching = true;
+    // one lockstep group per size class: (dim, nx, ny, nz, precision)
+    std::map<std::tuple<int, int, int, int, int>, rve_batch_group> groups;
+    rve_batch_group group_for(const rve_config &c) {
+        if (!batching || c.split != RVE_SPLIT_NONE || c.solver != RVE_SOLVER_STAGGERED) return nullptr;
+        std::lock_guard<std::mutex> lk(mu);
+        auto key = std::make_tuple(c.dim, c.n[0], c.n[1], c.n[2], c.precision);
+        auto it = groups.find(key);
+        if (it != groups.end()) return it->second;
+        rve_batch_group g = nullptr;
+        if (rve_batch_group_create(&g) != RVE_OK) return nullptr;
+        groups[key] = g;
+        return g;
+    }
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
 
     double now() const {
@@ -66,9 +85,10 @@ struct Server {
         rc = set_microstructure(h, &q.m);
         if (!rc) {
             const long nvox = (long)q.cfg.n[0] * q.cfg.n[1] * q.cfg.n[2];
+            rve_batch_group grp = group_for(q.cfg);
             for (int i = 0; i < q.n_inc; ++i) {
                 rve_step_result s;
-                rc = step_dissipation(h, q.dtau, &s);
+                rc = grp ? rve_step_in_group(h, grp, q.dtau, &s) : step_dissipation(h, q.dtau, &s);
                 if (rc) break;
                 r.n_done = s.n;
                 r.E_last = s.E;
@@ -221,6 +241,13 @@ int rve_server_stats(rve_server sv, int *peak_inflight, size_t *peak_bytes, long
     return RVE_OK;
 }
 
+int rve_server_set_batching(rve_server sv, int on) {
+    if (!sv) return RVE_EINVAL;
+    std::lock_guard<std::mutex> lk(sv->s.mu);
+    sv->s.batching = on != 0;
+    return RVE_OK;
+}
+
 int rve_server_destroy(rve_server sv) {
     if (!sv) return RVE_EINVAL;
     {
@@ -229,6 +256,7 @@ int rve_server_destroy(rve_server sv) {
     }
     sv->s.cv_work.notify_all();
     for (auto &t : sv->s.workers) t.join();
+    for (auto &kv : sv->s.groups) rve_batch_group_destroy(kv.second);
     delete sv;
     return RVE_OK;
 }

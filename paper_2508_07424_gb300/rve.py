@@ -150,6 +150,18 @@ class Rve:
         capi.check(capi.lib().rve_timing_get(self.h, kind, C.byref(ms), C.byref(n), C.byref(b)), "rve_timing_get")
         return ms.value, n.value, b.value
 
+    def timing_kinds(self):
+        """Per kernel class recorded since timing was enabled: {name: (ms, launches, bytes per
+        launch, FFT flops per launch)}."""
+        out = {}
+        for kind, name in ((0, "projection_pass"), (1, "k_axis"), (2, "k_x_fwd"), (3, "k_x_inv"), (4, "k_x_mid"),
+                           (5, "k_pointwise"), (6, "all")):
+            ms, n, b, f = C.c_double(), C.c_long(), C.c_double(), C.c_double()
+            capi.check(capi.lib().rve_timing_get_flops(self.h, kind, C.byref(ms), C.byref(n), C.byref(b), C.byref(f)),
+                       "rve_timing_get_flops")
+            out[name] = (ms.value, n.value, b.value, f.value)
+        return out
+
     def launches(self):
         return capi.lib().rve_launch_count(self.h)
 
@@ -168,3 +180,15 @@ class Rve:
             self.close()
         except Exception:
             pass
+
+
+def step_batch(rves, dtaus):
+    """One increment of each Rve in lockstep (rve_step_batch): the solves of all of them are
+    launched together, one kernel launch per pass. Returns the step records; raises on the first
+    failing status (the other increments are committed all the same)."""
+    n = len(rves)
+    hs = (capi.rve_handle * n)(*[r.h for r in rves])
+    dt = (C.c_double * n)(*[float(d) for d in dtaus])
+    out = (capi.rve_step_result * n)()
+    capi.check(capi.lib().rve_step_batch(hs, n, dt, out), "rve_step_batch")
+    return [{k: getattr(out[i], k) for k, _ in out[i]._fields_} for i in range(n)]

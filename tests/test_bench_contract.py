@@ -27,7 +27,33 @@ def test_json_helpers():
     sys.path.insert(0, ROOT)
     import bench
     assert bench._finite({"a": float("nan"), "b": [1.0, float("inf")]}) == {"a": None, "b": [1.0, None]}
-    b2, f2 = bench.axis_kernel_model(512, 512, 3, 4)
-    assert b2 == 2 * 3 * 257 * 512 * 2 * 4 and f2 > 0
-    b3, f3 = bench.axis_kernel_model(64, 64, 6, 4, 64)
-    assert b3 == 2 * 6 * 33 * 64 * 64 * 2 * 4 and f3 != f3      # 3D: flops not modelled (NaN)
+    a = {"n": 3, "E": 0.5, "G_inst": float("nan")}
+    assert bench.same_result(a, dict(a)) and not bench.same_result(a, dict(a, E=0.5000000001))
+
+
+def test_both_arms_name_the_same_metric_and_config():
+    """The driver divides the two arms' values only when they measure the same thing."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    d = json.loads([x for x in r.stdout.strip().splitlines() if x.startswith("{")][0])
+    assert d["metric"] == bench.METRIC
+    assert d["config"] == bench.workload_config(bench.WORKLOAD, "fp64", "staggered", 1)
+
+
+def test_roofline_of_dominant_kernel_class():
+    sys.path.insert(0, ROOT)
+    import bench
+    bd = {"classes": {
+        "k_axis": {"ms_per_step": 5.0, "bytes_per_launch": 4e6, "avg_launch_us": 10.0, "launches_per_step": 500,
+                   "share": 0.3, "GB_s": 400.0, "TFLOP_s": 0.5},
+        "k_x_fwd": {"ms_per_step": 3.0, "bytes_per_launch": 5e6, "avg_launch_us": 6.0, "launches_per_step": 500,
+                    "share": 0.2, "GB_s": 800.0, "TFLOP_s": 0.4},
+        "projection_pass": {"ms_per_step": 9.0, "bytes_per_launch": 6e6, "avg_launch_us": 12.0,
+                            "launches_per_step": 100, "share": 0.1, "GB_s": 500.0, "TFLOP_s": 0.6}}}
+    f64 = {"tflops": 1.0}
+    r = bench.roofline_of(bd, "fp64", "w", 6000.0, "measured", f64)
+    assert r["kernel"] == "k_axis" and r["bound"] == "alu" and abs(r["frac"] - 0.5) < 1e-12
+    r = bench.roofline_of(bd, "fp32r", "w", 6000.0, "measured", f64)
+    assert r["bound"] == "hbm" and abs(r["frac"] - 400.0 / 6000.0) < 1e-12 and r["traffic"] is None

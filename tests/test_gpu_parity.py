@@ -10,6 +10,8 @@ order of rounding and in the CG formulation (symmetric strain vs displacement gr
 converged answers agree to about the solver tolerance times the conditioning of each solve; the
 per-step bounds below are 1e-10 (fields, energies) unless a comment says otherwise.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -32,7 +34,7 @@ def cap():
 def _pair(name, **tol):
     from paper_2508_07424_gb300.rve import Rve
     w = synth.small_cases()[name]
-    kw = dict(tol_mech=1e-13, tol_dmg=1e-13, tol_root=1e-13, tol_stag=1e-11)
+    kw = dict(tol_mech=1e-13, tol_dmg=1e-13, tol_root=1e-13, tol_stag=1e-12)
     kw.update(tol)
     model = S.Model(w.micro, S.params_from_workload(w, **kw))
     g = Rve.from_workload(w, tol_mech=kw["tol_mech"], tol_dmg=kw["tol_dmg"], tol_root=kw["tol_root"],
@@ -100,13 +102,14 @@ def test_increments_from_the_same_start(cap, name):
         r = g.step(w.dtau)
         o = st.curve[-1]
         for k in ("E", "Sigma", "D", "T", "Gamma"):
-            assert abs(r[k] - o[k]) <= 1e-9 * abs(o[k]), (k, r[k], o[k])
-        assert abs(r["Emec"] - o["Emec"]) <= 1e-9 * abs(o["Emec"])
-    assert rel(g.get(cap.RVE_FIELD_PHI), st.phi) < 1e-9
-    assert rel(g.get(cap.RVE_FIELD_H), st.H) < 1e-9
-    assert rel(g.get(cap.RVE_FIELD_EPS), sym_components(st.eps, model.d)) < 1e-9
+            assert abs(r[k] - o[k]) <= 1e-10 * abs(o[k]), (k, r[k], o[k])
+        assert abs(r["Emec"] - o["Emec"]) <= 1e-10 * abs(o["Emec"])
+        assert not (r["flags"] & (cap.RVE_STEP_STAGNATED | cap.RVE_STEP_UNCONVERGED)), r["flags"]
+    assert rel(g.get(cap.RVE_FIELD_PHI), st.phi) < 1e-10
+    assert rel(g.get(cap.RVE_FIELD_H), st.H) < 1e-10
+    assert rel(g.get(cap.RVE_FIELD_EPS), sym_components(st.eps, model.d)) < 1e-10
     sig = model.stress(st.eps, st.phi)
-    assert rel(g.get(cap.RVE_FIELD_SIGMA), sym_components(sig, model.d)) < 1e-9
+    assert rel(g.get(cap.RVE_FIELD_SIGMA), sym_components(sig, model.d)) < 1e-10
 
 
 def test_increment_from_injected_oracle_state(cap):
@@ -124,8 +127,8 @@ def test_increment_from_injected_oracle_state(cap):
     r = g.step(w.dtau)
     o = st2.curve[-1]
     for k in ("E", "Sigma", "D", "T"):
-        assert abs(r[k] - o[k]) <= 1e-9 * abs(o[k]), (k, r[k], o[k])
-    assert rel(g.get(cap.RVE_FIELD_PHI), st2.phi) < 1e-9
+        assert abs(r[k] - o[k]) <= 1e-10 * abs(o[k]), (k, r[k], o[k])
+    assert rel(g.get(cap.RVE_FIELD_PHI), st2.phi) < 1e-10
 
 
 def test_checkpoint_round_trip_is_bit_exact(cap):
@@ -185,7 +188,12 @@ def test_run_to_fracture_load_curve(cap):
     Gg = V / Ag * (rs[-2]["T"] - 0.5 * rs[-2]["Sigma"] * rs[-2]["E"])
     Go = V / Ag * (st.curve[-2]["T"] - 0.5 * st.curve[-2]["Sigma"] * st.curve[-2]["E"])
     assert abs(Gg - Go) < 1e-9 * Go
-    assert g.toughness() > 0 and G > 0
+    # the library's own call on the state of F - 1 (scalars injected from this run's increment F - 1)
+    sc = g.scalars()
+    g.set_scalars(n=rs[-2]["n"], E=rs[-2]["E"], tau=rs[-2]["tau"], T=rs[-2]["T"], Sigma=rs[-2]["Sigma"],
+                  Sigma_max=sc["Sigma_max"], fractured=1)
+    assert abs(g.toughness() - Go) < 1e-9 * Go
+    assert G > 0
     # Eq. (Gmed) per increment. It divides the change of T by the change of Gamma, so the 1e-9
     # agreement of T and Gamma becomes ~1e-9 Gamma / dGamma; 1e-6 covers the smallest step here.
     gi = S.instantaneous_toughness(model_of(w, p), st.Gamma0, st.curve)
@@ -202,11 +210,85 @@ def model_of(w, p):
     return S.Model(w.micro, p)
 
 
+def _uniform_to_fracture(precision, dtau_frac=0.01):
+    """A homogeneous uncracked 16^2 cell stays on the uniform branch (closed form, pin P7) until it
+    breaks: the fracture increment is unique, so G of Eq. (JaviGc) is well posed on both sides."""
+    from paper_2508_07424_gb300.rve import Rve
+    w = synth.Workload(synth.homogeneous((16, 16)), ell=2.0, precision=precision)
+    w.dtau = dtau_frac * 256
+    p = S.params_from_workload(w, tol_stag=1e-12, tol_root=1e-14)
+    model, st, G = S.run(w, n_inc=200, params=p)
+    kw = dict(tol_mech=1e-13, tol_dmg=1e-13, tol_root=1e-13, tol_stag=1e-12) if precision == "fp64" else FP32R_TOLS
+    g = Rve.from_workload(w, **kw)
+    rs = []
+    for _ in range(200):
+        rs.append(g.step(w.dtau))
+        if rs[-1]["fractured"]:
+            break
+    return w, model, st, G, g, rs
+
+
+def test_toughness_call_on_a_well_posed_fracture(cap):
+    """effective_toughness() through the C ABI against the oracle's toughness() (Eqs. (JaviGc),
+    (ABC)) and against the closed form of the uniform branch, at 1e-10."""
+    w, model, st, G, g, rs = _uniform_to_fracture("fp64")
+    assert st.fractured and rs[-1]["fractured"] and rs[-1]["n"] == st.n > 10
+    Gg = g.toughness()
+    assert abs(Gg - G) <= 1e-10 * G, (Gg, G)
+    # closed form: phi_n = sqrt(2 l tau_n / (Gc V)), E_n = sqrt(Gc phi / (l (1 - phi) M)),
+    # Sigma_n = g(phi) M E, T by the trapezoid rule, G = V / A_g (T - Sigma E / 2), A_g = nx
+    M = synth.iso_constants(1.0, 0.3)[0]
+    V, ell, k = 256.0, 2.0, 1e-6
+    T, S0, E0 = 0.0, 0.0, 0.0
+    for n in range(1, st.n + 1):
+        phi = math.sqrt(2 * ell * n * w.dtau / V)
+        E = math.sqrt(phi / (ell * (1 - phi) * M))
+        Sg = ((1 - phi) ** 2 + k) * M * E
+        T += 0.5 * (Sg + S0) * (E - E0)
+        S0, E0 = Sg, E
+    Gc_ = V / 16.0 * (T - 0.5 * S0 * E0)
+    assert abs(Gg - Gc_) <= 1e-10 * Gc_, (Gg, Gc_)
+
+
+def test_fp32r_toughness_within_half_a_percent(cap):
+    """The FP32 path with iterative refinement to fracture: effective_toughness() within 0.5% of
+    the FP64 oracle (the accuracy target of the FP32 path), on the well-posed uniform fracture and
+    at the last well-posed increment of the cracked 16^2 plate."""
+    w, model, st, G, g, rs = _uniform_to_fracture("fp32r")
+    assert rs[-1]["fractured"] and abs(rs[-1]["n"] - st.n) <= 1
+    assert abs(g.toughness() - G) <= 5e-3 * G, (g.toughness(), G)
+    from paper_2508_07424_gb300.rve import Rve
+    crack = synth.Crack(synth.CRACK_CTE, row=8, x0=0, length=4, phi_M=0.8)
+    w = synth.Workload(synth.homogeneous((16, 16), crack=crack), ell=2.0, n_inc=60, precision="fp32r")
+    w.dtau = 1.5 * 12 / 30
+    p = S.params_from_workload(w, tol_stag=1e-9)
+    _, st, _ = S.run(w, params=p)
+    g = Rve.from_workload(w, **FP32R_TOLS)
+    rs = []
+    for _ in range(60):
+        rs.append(g.step(w.dtau))
+        if rs[-1]["fractured"]:
+            break
+    assert rs[-1]["fractured"] and rs[-1]["n"] == st.n
+    V, Ag = 256.0, 12.0
+    o = st.curve[-2]
+    G_o = V / Ag * (o["T"] - 0.5 * o["Sigma"] * o["E"])
+    r = rs[-2]
+    G_g = V / Ag * (r["T"] - 0.5 * r["Sigma"] * r["E"])
+    assert abs(G_g - G_o) <= 5e-3 * G_o, (G_g, G_o)
+
+
 # ---- FP32 with iterative refinement against the FP64 oracle --------------------------------------
-# Field arithmetic (FFTs, projection, stress, CG vectors) is FP32; dot products, energies and the
-# control search are FP64. The solves stop at 1e-6 relative residuals (the FP32 floor is ~1e-7),
-# the staggered loop at 1e-5, so increment scalars agree with the FP64 oracle to ~1e-5 and the
-# toughness, an integral of them, well inside the 0.5% target.
+# Field arithmetic (FFTs, projection, stress, CG vectors) is FP32; dot products, energies, the
+# control search and the load curve are FP64, and the equilibrium is refined on its FP64 residual
+# with an FP64 solution (each correction projected onto compatible strains). The tolerances are
+# those of the benchmark's FP32R runs: equilibrium 1e-8 on the FP64 residual, damage and staggered
+# loop 1e-6. The scalars of the first increment are the least accurate (E and Sigma ~1e-5 in the
+# 32^2 polycrystal, T = E Sigma / 2 then 1.7e-5): the bound on them is 3e-5. Measured against the FP64 oracle: increment scalars ~1e-6 to 3e-6, stress ~1e-6 to
+# 2e-6, inside the targets (stress 1e-5, toughness 0.5 %).
+FP32R_TOLS = dict(tol_mech=1e-8, tol_dmg=1e-6, tol_root=1e-8, tol_stag=1e-6)
+
+
 @pytest.mark.parametrize("name", ["fibre64x16", "poly32", "poly3d", "plate3d"])
 def test_fp32r_increments_against_fp64_oracle(cap, name):
     from paper_2508_07424_gb300.rve import Rve
@@ -214,32 +296,36 @@ def test_fp32r_increments_against_fp64_oracle(cap, name):
     model = S.Model(w.micro, S.params_from_workload(w, tol_stag=1e-10))
     st = S.init_state(model)
     w32 = synth.replace(w, precision="fp32r")
-    g = Rve.from_workload(w32)
+    g = Rve.from_workload(w32, **FP32R_TOLS)
     for _ in range(3):
         st, _ = S.increment(model, st, w.dtau)
         r = g.step(w.dtau)
         o = st.curve[-1]
         for k in ("E", "Sigma", "D", "T"):
-            assert abs(r[k] - o[k]) <= 2e-5 * abs(o[k]), (k, r[k], o[k])
+            assert abs(r[k] - o[k]) <= 3e-5 * abs(o[k]), (k, r[k], o[k])
     sig = sym_components(model.stress(st.eps, st.phi), model.d)
-    assert rel(g.get(cap.RVE_FIELD_SIGMA), sig) < 1e-4
-    assert rel(g.get(cap.RVE_FIELD_PHI), st.phi) < 1e-4
+    assert rel(g.get(cap.RVE_FIELD_SIGMA), sig) < 1e-5
+    assert rel(g.get(cap.RVE_FIELD_PHI), st.phi) < 1e-5
 
 
 def test_fp32r_equilibrium_solve(cap):
     from paper_2508_07424_gb300.rve import Rve
     w = synth.small_cases()["poly32"]
     model = S.Model(w.micro, S.params_from_workload(w, tol_mech=1e-13))
-    g = Rve.from_workload(synth.replace(w, precision="fp32r"))
+    g = Rve.from_workload(synth.replace(w, precision="fp32r"), tol_mech=1e-10)
     rng = np.random.default_rng(4)
-    phi = rng.uniform(0.0, 0.9, model.grid)
+    # the FP32 path holds phi in FP32; the oracle solves with that same (rounded) damage field, so
+    # the comparison sees the solver alone (the strain is sensitive to g(phi) where phi -> 0.9)
+    phi = rng.uniform(0.0, 0.9, model.grid).astype(np.float32).astype(np.float64)
     g.set(cap.RVE_FIELD_PHI, phi)
     g.mech_solve()
     F1, _ = S.mech_solve(model, phi, np.zeros((model.d, model.d) + model.grid))
     eps = model.fB + 0.5 * (F1 + np.swapaxes(F1, 0, 1))
     g_eps = sym_components(model.fB, model.d) + g.get(cap.RVE_FIELD_FLUCT1)
-    # FP32 residual floor 1e-6 x the conditioning of this random-damage RVE (contrast ~100)
-    assert rel(g_eps, sym_components(eps, model.d)) < 5e-5
+    # refinement on the FP64 residual with an FP64 solution: the strain is limited by its FP32
+    # copy (relative rounding 6e-8), not by the solver (measured 7e-8)
+    assert rel(g_eps, sym_components(eps, model.d)) < 5e-7
+    assert rel(g.get(cap.RVE_FIELD_PSI1), model.drive(eps)) < 1e-6
 
 
 # ---- spectral energy split (configs[0] model variant; plane strain) ------------------------------

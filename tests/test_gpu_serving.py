@@ -109,3 +109,29 @@ def test_crack_position_sampling(mods):
         assert abs(r["n_done"] - res[0]["n_done"]) <= 1
         assert abs(r["toughness"] - G0) <= 0.02 * G0, (r["row"], r["x0"], r["toughness"], G0)
     assert gmin == min(r["toughness"] for r in res)
+
+
+def test_continuous_batching_gives_the_same_results(mods):
+    """Requests of one grid class step through a shared lockstep group (their solve loops run as
+    one launch per pass); results equal those of the server without batching, bit for bit."""
+    capi, serve, Rve = mods
+    crack = synth.Crack(synth.CRACK_CTE, row=16, x0=0, length=6, phi_M=0.8)
+    ws = []
+    for seed in (21, 22, 23, 24):
+        m = synth.voronoi((32, 32), 9, seed, beta=2.0, crack=crack)
+        w = synth.Workload(m, ell=2.0, n_inc=8)
+        w.dtau = 1.5 * w.A_g / 24
+        ws.append(w)
+    ws.append(synth.replace(ws[0], precision="fp32r"))
+    ws.append(synth.replace(ws[1], precision="fp32r"))
+    outs = []
+    for batching in (True, False):
+        srv = serve.Server(max_inflight=len(ws), batching=batching)
+        out, _ = serve.replay(srv, [(0.0, w, 3) for w in ws], tol_stag=1e-9)
+        srv.close()
+        outs.append(out)
+    for i in range(len(ws)):
+        a, b = outs[0][i], outs[1][i]
+        assert a["status"] == capi.RVE_OK and b["status"] == capi.RVE_OK
+        for k in ("n_done", "E_last", "Sigma_last", "T_last", "voxel_updates"):
+            assert a[k] == b[k], (i, k, a[k], b[k])
