@@ -267,7 +267,7 @@ def fp64_peak(torch, stream):
             "8 independent FMA chains per thread, CUDA events; best of 3 launches of ~1.5 s"}
 
 
-KERNEL_CLASSES = ("k_axis", "k_x_fwd", "k_x_inv", "k_x_mid", "k_pointwise")
+KERNEL_CLASSES = ("k_axis", "k_x_fwd", "k_x_inv", "k_x_mid", "k_pointwise", "fp64_residual")
 
 
 def same_result(a, b):
@@ -314,7 +314,9 @@ def kernel_breakdown(torch, stream, g, w, state, steps):
 
 def roofline_of(bd, precision, workload, hbm_peak, hbm_src, f64):
     """Roofline of the dominant kernel class (largest time per increment in the replay)."""
-    cls = {k: v for k, v in bd["classes"].items() if k != "projection_pass"}
+    # single kernel templates only: the projection pass is a subset of k_axis, the FP64 residual
+    # class of the FP32 path mixes x and column passes
+    cls = {k: v for k, v in bd["classes"].items() if k not in ("projection_pass", "fp64_residual")}
     dom = max(cls, key=lambda k: cls[k]["ms_per_step"])
     c = cls[dom]
     traffic = TRAFFIC.get((workload, precision, dom))
@@ -451,7 +453,7 @@ def run_gpu(args):
     if world == 1 and w.micro.dim == 2:
         out["cufft_reference"] = cufft_reference(torch, stream, g, w, args.precision)
     g.close()
-    if world == 1 and args.workload == WORKLOAD and args.precision == "fp64":
+    if world == 1 and args.workload == WORKLOAD and args.precision == "fp64" and not args.no_side:
         side = timed_leg(torch, stream, make_workload(rank, "fp32r", args.workload), "fp32r", args, 1, flush,
                          e2e=False)
         out["fp32r_side_by_side"] = {
@@ -769,6 +771,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the lockstep batching legs")
+    ap.add_argument("--no-side", action="store_true", help="skip the FP32R leg beside the FP64 headline")
     ap.add_argument("--workload", default=WORKLOAD, choices=list(WORKLOADS))
     ap.add_argument("--solver", default="staggered", choices=["staggered", "newton"],
                     help="increment solver: staggered fixed point (default) or the monolithic Newton of Sec. 4.1")

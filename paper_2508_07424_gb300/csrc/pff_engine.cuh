@@ -1241,7 +1241,7 @@ struct Engine : EngineBase {
         int th, bl; size_t sm; xcfg<U>(th, bl, sm);
         auto k = k_x_fwd<U, NC, Pro>;
         prep_smem(k, sm * NC);
-        cudaEvent_t e = tbeg(2, 0, xbytes<U>(NC, rw_words<Pro>()), xflops(NC));
+        cudaEvent_t e = tbeg(std::is_same<U, T>::value ? 2 : 7, 0, xbytes<U>(NC, rw_words<Pro>()), xflops(NC));
         k<<<bl, th, sm * NC, st>>>(g, pro, spec_of<U>(), tw_of<U>(g.nx), partials, s);
         CK(cudaGetLastError());
         tend(e);
@@ -1251,7 +1251,7 @@ struct Engine : EngineBase {
         int th, bl; size_t sm; xcfg<U>(th, bl, sm);
         auto k = k_x_inv<U, NC, Epi>;
         prep_smem(k, sm * NC);
-        cudaEvent_t e = tbeg(3, 0, xbytes<U>(NC, rw_words<Epi>()), xflops(NC));
+        cudaEvent_t e = tbeg(std::is_same<U, T>::value ? 3 : 7, 0, xbytes<U>(NC, rw_words<Epi>()), xflops(NC));
         k<<<bl, th, sm * NC, st>>>(g, spec_of<U>(), epi, tw_of<U>(g.nx), partials, s);
         CK(cudaGetLastError());
         tend(e);
@@ -1292,7 +1292,9 @@ struct Engine : EngineBase {
         const int nout = MODE == AX_FWD_OP_INV ? NCO : NCI;
         const int ntr = MODE == AX_FWD_OP_INV ? NCI + NCO : NCI;
         const double cols = (double)(g.nx / 2 + 1) * (ax == 1 ? g.nz : g.ny);
-        cudaEvent_t e = tbeg(1, timed ? 1 : 0, (double)(NCI + nout) * cols * L * sizeof(CU),
+        // the FP64 residual passes of the FP32 engine form their own class (7)
+        cudaEvent_t e = tbeg(std::is_same<U, T>::value ? 1 : 7, (timed && std::is_same<U, T>::value) ? 1 : 0,
+                             (double)(NCI + nout) * cols * L * sizeof(CU),
                              (double)ntr * cols * 5.0 * L * (ax == 1 ? g.ly : g.lz));
         k<<<grid, threads, sm, st>>>(g, ax, CW, spec_of<U>(), spec_of<U>(), op, tw_of<U>(L), s);
         CK(cudaGetLastError());
@@ -2640,7 +2642,7 @@ struct Engine : EngineBase {
         long cnt = 0;
         for (size_t i = 0; i < ev_used; ++i) {
             const EvMeta &m = ev_meta[i];
-            const bool take = kind == 0 ? m.proj != 0 : kind == 6 ? true : m.kind == kind;
+            const bool take = kind == 0 ? m.proj != 0 : kind == 6 ? true : m.kind == kind;  // 7: FP64 residual passes
             if (!take) continue;
             float t = 0.f;
             CK(cudaEventElapsedTime(&t, ev_pool[i].first, ev_pool[i].second));

@@ -285,12 +285,20 @@ __device__ __forceinline__ int brev_bits(int v, int bits) {
     return bits == 0 ? 0 : (int)(__brev((unsigned)v) >> (32 - bits));
 }
 __device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
-// Frequency index held at storage position p of a line of L points after wfft_fwd.
+// Frequency index held at storage position p of a line of L points after the forward transform.
+// R < 8 (wfft_fwd): p = l + S m holds brev_R(m) + R brev_S(l). R >= 8 (wfft2_fwd, S = 32 lanes in
+// G = 32 / R groups): p = l + 32 c holds brev_R(l / G) + R brev_R(c) + R^2 brev_G(l mod G).
 __device__ __forceinline__ int axis_freq(int p, int L) {
     const int R = axis_points_per_lane(L);
     const int lgR = ilog2(R), lgS = ilog2(L) - lgR;
-    const int m = p >> lgS, l = p & ((1 << lgS) - 1);
-    return brev_bits(m, lgR) + (brev_bits(l, lgS) << lgR);
+    if (R < 8) {
+        const int m = p >> lgS, l = p & ((1 << lgS) - 1);
+        return brev_bits(m, lgR) + (brev_bits(l, lgS) << lgR);
+    }
+    const int lgG = 5 - lgR;
+    const int lp = p & 31, c = p >> 5;
+    const int j = lp >> lgG, gg = lp & ((1 << lgG) - 1);
+    return brev_bits(j, lgR) + (brev_bits(c, lgR) << lgR) + (brev_bits(gg, lgG) << (2 * lgR));
 }
 
 __device__ __forceinline__ double2 shfl_xor_c(double2 v, int m) {
@@ -407,10 +415,136 @@ __device__ __forceinline__ void wfft_inv(C (&v)[R], int l, int S, int L, const C
     }
 }
 
+// In-register radix-2 stages over R values (compile-time twiddles w_{2h}^j = w_32^(16 j / h)).
+template <typename C, int R> __device__ __forceinline__ void regs_dif(C (&v)[R]) {
+#pragma unroll
+    for (int h = R / 2; h >= 1; h >>= 1) {
+#pragma unroll
+        for (int b = 0; b < R; b += 2 * h) {
+#pragma unroll
+            for (int j = 0; j < h; ++j) {
+                const C a = v[b + j], c = v[b + j + h];
+                v[b + j] = cadd(a, c);
+                const C d = csub(a, c);
+                v[b + j + h] = j == 0 ? d : cmul(d, w32<C>(j * (16 / h)));
+            }
+        }
+    }
+}
+template <typename C, int R> __device__ __forceinline__ void regs_dit(C (&v)[R]) {
+#pragma unroll
+    for (int h = 1; h < R; h <<= 1) {
+#pragma unroll
+        for (int b = 0; b < R; b += 2 * h) {
+#pragma unroll
+            for (int j = 0; j < h; ++j) {
+                const C t = j == 0 ? v[b + j + h] : cmul(v[b + j + h], conj_c(w32<C>(j * (16 / h))));
+                const C a = v[b + j];
+                v[b + j] = cadd(a, t);
+                v[b + j + h] = csub(a, t);
+            }
+        }
+    }
+}
+
+// Two-pass warp transform of a line of L = 32 R points (R >= 8), one line per warp: the lane
+// dimension (32 points) is split as 32 = G x R (G = 32 / R) so that most butterflies run in
+// registers instead of across lanes. Pass A: lane l holds x[l + 32 m]; R-point DFT over m,
+// twiddle w_L^(l k1). Transpose through the line's shared memory (rows of 32 + G elements, so
+// that the gathers hit distinct banks): lane (j, g) = (l / G, l mod G) takes the R values of
+// row j at columns g + G t. Pass B: R-point DFT over t, twiddle w_32^(g c), then log2 G stages
+// across the G lanes of a group. The result is in the order of axis_freq; `line` must have room
+// for L + 32 elements. Every lane of the warp must call it.
+template <typename C, int R>
+__device__ __forceinline__ void wfft2_fwd(C (&v)[R], C *line, int l, int L, const C *__restrict__ tw) {
+    constexpr int G = 32 / R, lgR = log2_of<R>::v, rs = 32 + G;
+    typedef typename real_of<C>::type Rt;
+    regs_dif<C, R>(v);
+#pragma unroll
+    for (int m = 1; m < R; ++m) {
+        const int k1 = (int)(__brev((unsigned)m) >> (32 - lgR));
+        v[m] = cmul(v[m], tw[(l * k1) & (L - 1)]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < R; ++m) line[m * rs + l] = v[m];
+    __syncwarp();
+    const int j = l / G, gg = l & (G - 1);
+#pragma unroll
+    for (int t = 0; t < R; ++t) v[t] = line[j * rs + gg + G * t];
+    regs_dif<C, R>(v);
+    if (G > 1) {
+#pragma unroll
+        for (int c = 1; c < R; ++c) {
+            const int cc = (int)(__brev((unsigned)c) >> (32 - lgR));
+            v[c] = cmul(v[c], tw[(gg * cc * R) & (L - 1)]);
+        }
+        for (int h = G >> 1; h >= 1; h >>= 1) {
+            const bool upper = (gg & h) != 0;
+            const Rt sg = upper ? (Rt)-1 : (Rt)1;
+            C w = tw[(gg & (h - 1)) * (L / (2 * h))];
+            if (!upper) { w.x = (Rt)1; w.y = (Rt)0; }
+#pragma unroll
+            for (int m = 0; m < R; ++m) {
+                const C o = shfl_xor_c(v[m], h);
+                C t;
+                t.x = fma(sg, v[m].x, o.x);
+                t.y = fma(sg, v[m].y, o.y);
+                v[m] = cmul(t, w);
+            }
+        }
+    }
+}
+template <typename C, int R>
+__device__ __forceinline__ void wfft2_inv(C (&v)[R], C *line, int l, int L, const C *__restrict__ tw) {
+    constexpr int G = 32 / R, lgR = log2_of<R>::v, rs = 32 + G;
+    typedef typename real_of<C>::type Rt;
+    const int j = l / G, gg = l & (G - 1);
+    if (G > 1) {
+        for (int h = 1; h < G; h <<= 1) {
+            const bool upper = (gg & h) != 0;
+            const Rt sg = upper ? (Rt)-1 : (Rt)1;
+            C w = conj_c(tw[(gg & (h - 1)) * (L / (2 * h))]);
+            if (!upper) { w.x = (Rt)1; w.y = (Rt)0; }
+#pragma unroll
+            for (int m = 0; m < R; ++m) {
+                const C send = cmul(v[m], w);
+                const C o = shfl_xor_c(send, h);
+                v[m].x = fma(sg, send.x, o.x);
+                v[m].y = fma(sg, send.y, o.y);
+            }
+        }
+#pragma unroll
+        for (int c = 1; c < R; ++c) {
+            const int cc = (int)(__brev((unsigned)c) >> (32 - lgR));
+            v[c] = cmul(v[c], conj_c(tw[(gg * cc * R) & (L - 1)]));
+        }
+    }
+    regs_dit<C, R>(v);
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < R; ++t) line[j * rs + gg + G * t] = v[t];
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = line[m * rs + l];
+#pragma unroll
+    for (int m = 1; m < R; ++m) {
+        const int k1 = (int)(__brev((unsigned)m) >> (32 - lgR));
+        v[m] = cmul(v[m], conj_c(tw[(l * k1) & (L - 1)]));
+    }
+    regs_dit<C, R>(v);
+}
+
 // Padding of a shared-memory line (complex elements): with CW columns read per row, the rows of
 // one 128-byte phase of a warp access land on distinct banks.
 template <typename C> __host__ __device__ constexpr int axis_line_pad(int CW) {
     return (int)(128 / sizeof(C)) / CW;
+}
+// Stride of a shared-memory line: L plus the padding, plus room for the transposition of the
+// two-pass transform where it is used (R >= 8; 32 is a multiple of the bank period, so the
+// padding keeps its effect).
+template <typename C> __host__ __device__ constexpr int axis_line_stride(int L, int CW) {
+    return L + axis_line_pad<C>(CW) + (axis_points_per_lane(L) >= 8 ? 32 : 0);
 }
 
 // Transform the lines [0, nlines) of the tile, one line per lane group of S lanes, looping over
@@ -428,8 +562,13 @@ __device__ __forceinline__ void axis_lines(C *s, int nlines, int LS, int L, cons
         C v[R];
 #pragma unroll
         for (int m = 0; m < R; ++m) v[m] = p[l + S * m];
-        if constexpr (INV) wfft_inv<C, R>(v, l, S, L, tw);
-        else wfft_fwd<C, R>(v, l, S, L, tw);
+        if constexpr (R >= 8) {  // S = 32: one line per warp, every lane of it valid or not
+            if constexpr (INV) wfft2_inv<C, R>(v, p, l, L, tw);
+            else wfft2_fwd<C, R>(v, p, l, L, tw);
+        } else {
+            if constexpr (INV) wfft_inv<C, R>(v, l, S, L, tw);
+            else wfft_fwd<C, R>(v, l, S, L, tw);
+        }
         __syncwarp();
         if (valid) {
 #pragma unroll
@@ -457,7 +596,7 @@ __device__ __forceinline__ void axis_body(const Geom &g, int axis, int CW,
     const int L = axis == 1 ? g.ny : g.nz;
     const int lgL = axis == 1 ? g.ly : g.lz;
     const int lgCW = ilog2(CW);
-    const int LS = L + axis_line_pad<C>(CW);
+    const int LS = axis_line_stride<C>(L, CW);
     const int kx0 = blockIdx.x * CW;
     const int other = blockIdx.y;
     const long long lstride = axis == 1 ? (long long)g.Px : (long long)g.Px * g.ny;
@@ -551,7 +690,7 @@ template <typename C> inline void axis_shape(int L, int NM, int CW, int &threads
     if (w > wmax) w = wmax;
     if (w < 1) w = 1;
     threads = (int)(32 * w);
-    smem = (size_t)NM * CW * (size_t)(L + axis_line_pad<C>(CW)) * sizeof(C);
+    smem = (size_t)NM * CW * (size_t)axis_line_stride<C>(L, CW) * sizeof(C);
 }
 
 template <typename T, class Op>
