@@ -150,11 +150,12 @@ def make_workload(rank, precision, name=WORKLOAD):
 
 def solver_tols(precision):
     """Solver tolerances of the benchmark runs. FP32R: the equilibrium is refined on its FP64
-    residual to 1e-8, the FP32 damage solve and the staggered loop stop at 1e-6 (the settings
+    residual to 1e-7, the FP32 damage solve, the control root and the staggered loop stop at
+    1e-6 / 1e-7 / 1e-6 (the settings
     whose accuracy the FP32R parity tests check against the FP64 oracle)."""
     if precision == "fp64":
         return dict(tol_stag=1e-8)
-    return dict(tol_mech=1e-8, tol_dmg=1e-6, tol_root=1e-8, tol_stag=1e-6)
+    return dict(tol_mech=1e-7, tol_dmg=1e-6, tol_root=1e-7, tol_stag=1e-6)
 
 
 def _finite(obj):
@@ -341,6 +342,22 @@ def roofline_of(bd, precision, workload, hbm_peak, hbm_src, f64):
     return roof
 
 
+def nvtx_push(name):
+    try:
+        import torch
+        torch.cuda.nvtx.range_push(name)
+    except Exception:  # an NVTX-less build: the range is only a profiling aid
+        pass
+
+
+def nvtx_pop():
+    try:
+        import torch
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
 def timed_leg(torch, stream, w, precision, args, world, flush, e2e=True):
     """Warm-up, K device-timed increments, the kernel breakdown and the end-to-end replay of the
     same increments for one RVE in one precision."""
@@ -364,12 +381,14 @@ def timed_leg(torch, stream, w, precision, args, world, flush, e2e=True):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     results = []
     torch.cuda.synchronize()
+    nvtx_push("timed_increments")  # lets a profiler select exactly the timed launches
     for i in range(args.steps):
         flush.fill_(float(i))
         ev[i][0].record(stream)
         results.append(g.step(w.dtau))
         ev[i][1].record(stream)
     torch.cuda.synchronize()
+    nvtx_pop()
     if world > 1:
         torch.distributed.barrier()
     ms = sum(a.elapsed_time(b) for a, b in ev)
@@ -421,7 +440,10 @@ def run_gpu(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     f64 = fp64_peak(torch, stream)
     w = make_workload(rank, args.precision, args.workload)
+    legs = {}
+    t_leg = time.perf_counter()
     leg = timed_leg(torch, stream, w, args.precision, args, world, flush, e2e=not args.no_e2e)
+    legs["main"] = time.perf_counter() - t_leg
     tot_ms, tot_vu = aggregate_over_ranks(leg["ms"], leg["vu"], world, "cuda")
     if rank != 0:
         leg["g"].close()
@@ -454,8 +476,10 @@ def run_gpu(args):
         out["cufft_reference"] = cufft_reference(torch, stream, g, w, args.precision)
     g.close()
     if world == 1 and args.workload == WORKLOAD and args.precision == "fp64" and not args.no_side:
+        t_leg = time.perf_counter()
         side = timed_leg(torch, stream, make_workload(rank, "fp32r", args.workload), "fp32r", args, 1, flush,
                          e2e=False)
+        legs["fp32r_side"] = time.perf_counter() - t_leg
         out["fp32r_side_by_side"] = {
             "value": side["vu"] / (side["ms"] * 1e-3), "unit": "voxel-updates/s", "ms_per_step": side["ms"] / args.steps,
             "dtype": "f32", "steps": args.steps, "warmup": args.warmup, "clocks": side["clocks"],
@@ -467,20 +491,29 @@ def run_gpu(args):
     if not args.no_batch and world == 1 and args.workload == WORKLOAD:
         import synth
         ws = [make_workload(r, "fp32r", WORKLOAD) for r in range(8)]
-        out["batched_2d_fibre512_fp32r"] = batched_leg(torch, ws, "fp32r", args.warmup, args.steps,
+        t_leg = time.perf_counter()
+        out["batched_2d_fibre512_fp32r"] = batched_leg(torch, ws, "fp32r", 2, min(args.steps, 10),
                                                        solver_tols("fp32r"))
+        legs["batched_2d"] = time.perf_counter() - t_leg
         out["batched_2d_fibre512_fp32r"]["what"] = ("8 fibre composites 512^2 (seeds 1-8), FP32R, one lockstep batch "
                                                     "(one launch per pass for all 8)")
         ws3 = synth.batched_3d_polycrystals()
-        out["batched_3d_polycrystals"] = batched_leg(torch, ws3, "fp32r", args.warmup, min(args.steps, 5),
+        t_leg = time.perf_counter()
+        out["batched_3d_polycrystals"] = batched_leg(torch, ws3, "fp32r", 1, min(args.steps, 3),
                                                      solver_tols("fp32r"))
+        legs["batched_3d"] = time.perf_counter() - t_leg
         out["batched_3d_polycrystals"]["what"] = WORKLOADS["batched_3d_polycrystals"]
     if not args.no_cpu_baseline and world == 1 and args.workload == WORKLOAD:
+        t_leg = time.perf_counter()
         out["cpu_baseline"] = cpu_baseline(args)
+        legs["cpu_baseline"] = time.perf_counter() - t_leg
     if args.workload == "homogeneous_plate_64" and world == 1:
         out["toughness_run"] = toughness_run(args, stream)
     if not args.no_serve and world == 1 and args.workload == WORKLOAD:
+        t_leg = time.perf_counter()
         out["serving"] = serving(args)
+        legs["serving"] = time.perf_counter() - t_leg
+    out["leg_wall_s"] = {k: round(v, 1) for k, v in legs.items()}
     return out
 
 
@@ -607,7 +640,7 @@ def serving(args):
     from paper_2508_07424_gb300 import serve
     from paper_2508_07424_gb300.rve import Rve
     sizes2d, sizes3d = ((64, 128, 256, 512, 1024), (32, 64, 128)) if args.serve_sizes == "full" else \
-        ((64, 128, 256, 512), (32,))
+        ((64, 128, 256), (32,))
     ws = synth.serving_mix(count=args.serve_requests, n_inc=args.serve_inc, sizes2d=sizes2d, sizes3d=sizes3d)
 
     def one_by_one(precision):
@@ -664,7 +697,7 @@ def serving(args):
         sizes[k] = sizes.get(k, 0) + 1
     return {"requests": len(ws), "increments_per_request": args.serve_inc, "grids": sizes,
             "mix": ("the serving stream's grids: 2D {64..1024}^2 and 3D {32..128}^3" if args.serve_sizes == "full"
-                    else "bounded subset of the serving stream: 2D {64..512}^2 and 3D 32^3") +
+                    else "bounded subset of the serving stream: 2D {64,128,256}^2 and 3D 32^3") +
                    ", fibre composites and polycrystals (synth.serving_mix, seed 4)",
             "arrivals": f"Poisson, rate 1.25 x FP32R one-by-one ({lam:.3f}/s), seed 40", "slots": 8,
             "server_fp32r_batched": batched, "server_fp32r_unbatched": unbatched,
@@ -775,8 +808,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=list(WORKLOADS))
     ap.add_argument("--solver", default="staggered", choices=["staggered", "newton"],
                     help="increment solver: staggered fixed point (default) or the monolithic Newton of Sec. 4.1")
-    ap.add_argument("--serve-requests", type=int, default=32)
-    ap.add_argument("--serve-inc", type=int, default=16)
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-inc", type=int, default=10)
     ap.add_argument("--serve-sizes", default="subset", choices=["subset", "full"],
                     help="grids of the serving mix: a bounded subset (default run) or the full range of the stream")
     args = ap.parse_args()

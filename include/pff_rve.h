@@ -192,10 +192,12 @@ int rve_step_batch(rve_handle *hs, int n, const double *dtau, rve_step_result *o
 /* A lockstep group for callers that step handles from threads of their own (the request server):
  * each rve_step_in_group call runs one increment of h like step_dissipation, and while it runs,
  * its solve loops are launched together with those of the other handles of the group that are
- * stepping at the same time (opportunistic batching; results stay bit-identical to stepping
- * alone). Handles of one group must share grid, precision and column tiles and use the staggered
- * solver without the split (RVE_EINVAL otherwise, checked per call for the handle's own
- * configuration). The group owns a coordinator thread and a stream; destroy it only when no
+ * stepping at the same time (opportunistic batching: a solve loop joins the running batch at its
+ * next chunk of iterations and leaves it as soon as it has converged; an idle group starts once
+ * every stepping handle has reached a loop or 200 us after the first one did; results stay
+ * bit-identical to stepping alone). Handles of one group must share grid, precision and column
+ * tiles and use the staggered solver without the split (RVE_EINVAL otherwise, checked per call
+ * for the handle's own configuration). The group owns a coordinator thread and a stream; destroy it only when no
  * rve_step_in_group call on it is running. */
 typedef struct rve_batch_group_s *rve_batch_group;
 int rve_batch_group_create(rve_batch_group *out);

@@ -3,18 +3,19 @@
 // Each RVE keeps its own engine, buffers, stream and host control (the staggered loop, the
 // control search, Anderson mixing), run in a host thread of its own. When a thread reaches the
 // iteration loop of a solve (the equilibrium CG or the damage PCG), it hands the loop to the
-// Batcher as a LoopReq and waits. Once every participating thread is either waiting or done, the
-// Batcher's coordinator groups the waiting loops by kind and runs each group as batched
-// launches: one kernel launch per pass serves every RVE of the group (blockIdx.z selects the
-// RVE), in chunks of iterations, until every RVE's own scalar block says done. An RVE that has
-// converged skips its share of the work (its kernels test its done flag), so each RVE performs
-// exactly the iterations it would perform alone, with the same arithmetic and the same reduction
-// order: its results are bit-identical to stepping it alone.
+// Batcher as a LoopReq and waits. The Batcher's coordinator groups the loops it holds by kind and
+// runs them as batched launches: one kernel launch per pass serves every RVE of a kind
+// (blockIdx.z selects the RVE), one chunk of iterations at a time; after each chunk it releases
+// the loops whose own scalar block says done and admits the loops that have arrived. An RVE that
+// has converged skips its share of the work (its kernels test its done flag), so each RVE
+// performs exactly the iterations it would perform alone, with the same arithmetic and the same
+// reduction order: its results are bit-identical to stepping it alone.
 #pragma once
 
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <condition_variable>
 #include <map>
 #include <mutex>
@@ -44,7 +45,13 @@ struct LoopReq {
 
 class Batcher {
   public:
-    explicit Batcher(int device, int chunk = 8) : device_(device), chunk_(chunk) {
+    // When no loop is active, the first chunk waits for company. window_us < 0: until every
+    // participant is waiting or done (participants that advance together, as in rve_step_batch);
+    // window_us >= 0: at most that long after the first loop arrived (participants that advance
+    // independently, as in the request server, then do not stall on one another's host work).
+    // While loops are active, new ones join at the next chunk.
+    explicit Batcher(int device, int chunk = 8, double window_us = -1.0)
+        : device_(device), chunk_(chunk), window_us_(window_us) {
         cudaSetDevice(device_);
         err_ = cudaStreamCreateWithFlags(&st_, cudaStreamNonBlocking);
         coord_ = std::thread([this] { loop(); });
@@ -81,6 +88,7 @@ class Batcher {
         {
             std::unique_lock<std::mutex> lk(mu_);
             r->done = false;
+            if (waiting_.empty()) first_wait_ = std::chrono::steady_clock::now();
             waiting_.push_back(r);
             --running_;
             cv_coord_.notify_all();
@@ -91,59 +99,84 @@ class Batcher {
     }
 
   private:
+    // Continuous batching at chunk granularity: the coordinator keeps a set of active loops,
+    // admits the loops that arrived while the previous chunk ran, launches one chunk of
+    // iterations for every active loop (one launch per pass and kind, up to kMaxBatch RVEs per
+    // launch), reads every active loop's scalars back, and releases the loops that are done, so
+    // that a loop that converges early does not wait for the slowest one and a loop that
+    // arrives late does not wait for the running ones to finish. A loop's arithmetic does not
+    // depend on which other loops share its launches, so where it joins does not change its bits.
     void loop() {
         cudaSetDevice(device_);
+        std::vector<LoopReq *> active;
         for (;;) {
-            std::vector<LoopReq *> batch;
+            std::vector<LoopReq *> fresh;
             {
                 std::unique_lock<std::mutex> lk(mu_);
-                cv_coord_.wait(lk, [&] { return stop_ || (running_ == 0 && !waiting_.empty()); });
-                if (waiting_.empty()) return;  // stop requested and nothing left
-                batch.swap(waiting_);
+                if (active.empty()) {
+                    if (window_us_ < 0.0) {
+                        cv_coord_.wait(lk, [&] { return stop_ || (running_ == 0 && !waiting_.empty()); });
+                    } else {
+                        cv_coord_.wait(lk, [&] { return stop_ || !waiting_.empty(); });
+                        if (!waiting_.empty()) {
+                            const auto until = first_wait_ + std::chrono::microseconds((long)window_us_);
+                            cv_coord_.wait_until(lk, until, [&] { return stop_ || running_ == 0; });
+                        }
+                    }
+                    if (waiting_.empty()) return;  // stop requested and nothing left
+                }
+                fresh.swap(waiting_);
             }
-            execute(batch);
-            {
-                std::lock_guard<std::mutex> lk(mu_);
-                for (LoopReq *r : batch) r->done = true;
+            cudaError_t e = cudaSuccess;
+            for (LoopReq *r : fresh) {
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(st_, r->ready, 0);
+                active.push_back(r);
             }
-            cv_slots_.notify_all();
+            if (e == cudaSuccess) e = chunk(active);
+            // release the loops that are done (all of them after an error)
+            std::vector<LoopReq *> keep;
+            bool released = false;
+            for (LoopReq *r : active) {
+                if (e != cudaSuccess || r->h_sc->done) {
+                    cudaError_t f = e;
+                    if (f == cudaSuccess) f = cudaEventRecord(r->finished, st_);
+                    r->err = f;
+                    std::lock_guard<std::mutex> lk(mu_);
+                    r->done = true;
+                    released = true;
+                } else {
+                    keep.push_back(r);
+                }
+            }
+            active.swap(keep);
+            if (released) cv_slots_.notify_all();
         }
     }
-    void execute(std::vector<LoopReq *> &batch) {
-        // group by kind (launch function), at most kMaxBatch RVEs per launch
+    // One chunk of iterations for every active loop, then their scalars on the host.
+    cudaError_t chunk(std::vector<LoopReq *> &active) {
         std::map<void *, std::vector<LoopReq *>> kinds;
-        for (LoopReq *r : batch) kinds[(void *)r->launch].push_back(r);
+        for (LoopReq *r : active) kinds[(void *)r->launch].push_back(r);
+        cudaError_t e = cudaSuccess;
         for (auto &kv : kinds) {
             std::vector<LoopReq *> &all = kv.second;
-            for (size_t b0 = 0; b0 < all.size(); b0 += kMaxBatch) {
+            for (size_t b0 = 0; b0 < all.size() && e == cudaSuccess; b0 += kMaxBatch) {
                 std::vector<LoopReq *> grp(all.begin() + b0, all.begin() + std::min(all.size(), b0 + kMaxBatch));
-                cudaError_t e = cudaSuccess;
-                for (LoopReq *r : grp)
-                    if (e == cudaSuccess) e = cudaStreamWaitEvent(st_, r->ready, 0);
                 max_group_ = std::max(max_group_, (int)grp.size());
-                // chunks of iterations until every member is done (each member's kernels stop
-                // working once its own done flag is set; its iteration cap sets it at the latest)
-                for (int guard = 0; e == cudaSuccess; ++guard) {
-                    grp[0]->launch(grp, st_, chunk_);
-                    launches_ += chunk_;
-                    e = cudaGetLastError();
-                    for (LoopReq *r : grp)
-                        if (e == cudaSuccess) e = cudaMemcpyAsync(r->h_sc, r->sc, sizeof(Scal), cudaMemcpyDeviceToHost, st_);
-                    if (e == cudaSuccess) e = cudaStreamSynchronize(st_);
-                    bool all_done = true;
-                    for (LoopReq *r : grp) all_done = all_done && r->h_sc->done;
-                    if (all_done) break;
-                }
-                for (LoopReq *r : grp) {
-                    if (e == cudaSuccess) e = cudaEventRecord(r->finished, st_);
-                    r->err = e;
-                }
+                grp[0]->launch(grp, st_, chunk_);
+                launches_ += chunk_;
+                e = cudaGetLastError();
             }
         }
+        for (LoopReq *r : active)
+            if (e == cudaSuccess) e = cudaMemcpyAsync(r->h_sc, r->sc, sizeof(Scal), cudaMemcpyDeviceToHost, st_);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st_);
+        return e;
     }
 
     int device_;
     int chunk_;
+    double window_us_;
+    std::chrono::steady_clock::time_point first_wait_;
     cudaStream_t st_ = nullptr;
     cudaError_t err_ = cudaSuccess;
     std::mutex mu_;

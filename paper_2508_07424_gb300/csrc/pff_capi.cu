@@ -135,7 +135,9 @@ static int step_one_guarded(rve_handle h, double dtau, rve_step_result *out) {
 // ---- lockstep batching (pff_batch.cuh) -----------------------------------------------------------
 struct rve_batch_group_s {
     Batcher bat;
-    rve_batch_group_s(int dev) : bat(dev) {}
+    // groups serve threads that step independently (the request server): a batch also leaves
+    // once its first loop has waited 200 us, so no one stalls on another's host work
+    rve_batch_group_s(int dev) : bat(dev, 8, 200.0) {}
 };
 
 // One increment of a handle whose thread has joined the group: the solve loops go through the

@@ -938,9 +938,9 @@ struct Engine : EngineBase {
             // solve, the control root and the staggered test see FP32 fields and keep floors
             // at what those resolve.
             cfg.tol_mech = std::max(cfg.tol_mech, 1e-13);
-            cfg.tol_dmg = std::max(cfg.tol_dmg, 1e-8);
-            cfg.tol_root = std::max(cfg.tol_root, 1e-9);
-            cfg.tol_stag = std::max(cfg.tol_stag, 1e-8);
+            cfg.tol_dmg = std::max(cfg.tol_dmg, 1e-7);
+            cfg.tol_root = std::max(cfg.tol_root, 1e-7);  // D(phi) of FP32 fields resolves ~1e-7
+            cfg.tol_stag = std::max(cfg.tol_stag, 1e-7);
         }
         D = c.dim;
         NS = D == 2 ? 3 : 6;

@@ -282,11 +282,12 @@ def test_fp32r_toughness_within_half_a_percent(cap):
 # Field arithmetic (FFTs, projection, stress, CG vectors) is FP32; dot products, energies, the
 # control search and the load curve are FP64, and the equilibrium is refined on its FP64 residual
 # with an FP64 solution (each correction projected onto compatible strains). The tolerances are
-# those of the benchmark's FP32R runs: equilibrium 1e-8 on the FP64 residual, damage and staggered
-# loop 1e-6. The scalars of the first increment are the least accurate (E and Sigma ~1e-5 in the
-# 32^2 polycrystal, T = E Sigma / 2 then 1.7e-5): the bound on them is 3e-5. Measured against the FP64 oracle: increment scalars ~1e-6 to 3e-6, stress ~1e-6 to
-# 2e-6, inside the targets (stress 1e-5, toughness 0.5 %).
-FP32R_TOLS = dict(tol_mech=1e-8, tol_dmg=1e-6, tol_root=1e-8, tol_stag=1e-6)
+# those of the benchmark's FP32R runs: equilibrium 1e-7 on the FP64 residual, damage and staggered
+# loop 1e-6, control root 1e-7 (D of FP32 fields resolves ~1e-7; a tighter root makes the search
+# re-evaluate nearly the same D many times). Bounds: stress and damage fields 1e-5 (the stress
+# target); increment scalars 3e-5, because those of the first increment are the least accurate
+# (E and Sigma ~1e-5 in the 32^2 polycrystal, so T = E Sigma / 2 reaches 1.7e-5).
+FP32R_TOLS = dict(tol_mech=1e-7, tol_dmg=1e-6, tol_root=1e-7, tol_stag=1e-6)
 
 
 @pytest.mark.parametrize("name", ["fibre64x16", "poly32", "poly3d", "plate3d"])
