@@ -318,6 +318,17 @@ template <typename C> __device__ __forceinline__ C w32(int t);
 template <> __device__ __forceinline__ double2 w32<double2>(int t) { return c_w32d[t]; }
 template <> __device__ __forceinline__ float2 w32<float2>(int t) { return c_w32f[t]; }
 
+// d w_32^t and d conj(w_32^t) for a t known at compile time (the unrolled stages): t = 8 is -i,
+// a swap and a sign change instead of a complex multiply.
+template <typename C> __device__ __forceinline__ C mul_w32(const C &d, int t) {
+    if (t == 8) { C r; r.x = d.y; r.y = -d.x; return r; }
+    return cmul(d, w32<C>(t));
+}
+template <typename C> __device__ __forceinline__ C mul_w32c(const C &d, int t) {
+    if (t == 8) { C r; r.x = -d.y; r.y = d.x; return r; }
+    return cmul(d, conj_c(w32<C>(t)));
+}
+
 static inline cudaError_t axis_twiddles_init() {
     double2 d[32];
     float2 f[32];
@@ -329,6 +340,50 @@ static inline cudaError_t axis_twiddles_init() {
     cudaError_t e = cudaMemcpyToSymbol(c_w32d, d, sizeof(d));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w32f, f, sizeof(f));
     return e;
+}
+
+// Forward lane stage h over the R values of each lane: the lower lane of a pair keeps a + b, the
+// upper one (a - b) w. Both are t w~ with t = o + sgn v (sgn = -1 on the upper lane) and w~ = 1 on
+// the lower lane, so every lane runs the same instructions (no divergent halves). TW = false for
+// h = 1, whose twiddle is w_L^0 = 1 on both lanes.
+template <typename C, int R, bool TW>
+__device__ __forceinline__ void lane_stage_fwd(C (&v)[R], int l, int h, int L, const C *__restrict__ tw) {
+    typedef typename real_of<C>::type Rt;
+    const bool upper = (l & h) != 0;
+    const Rt sg = upper ? (Rt)-1 : (Rt)1;
+    C w;
+    if (TW) {
+        w = tw[(l & (h - 1)) * (L / (2 * h))];
+        if (!upper) { w.x = (Rt)1; w.y = (Rt)0; }
+    }
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+        const C o = shfl_xor_c(v[m], h);
+        C t;
+        t.x = fma(sg, v[m].x, o.x);
+        t.y = fma(sg, v[m].y, o.y);
+        v[m] = TW ? cmul(t, w) : t;
+    }
+}
+// Inverse lane stage h: the upper lane sends u = conj(w) b', the lower one a'; the lower lane keeps
+// a' + u, the upper one a' - u, i.e. o + sgn send with sgn = -1 on the upper lane.
+template <typename C, int R, bool TW>
+__device__ __forceinline__ void lane_stage_inv(C (&v)[R], int l, int h, int L, const C *__restrict__ tw) {
+    typedef typename real_of<C>::type Rt;
+    const bool upper = (l & h) != 0;
+    const Rt sg = upper ? (Rt)-1 : (Rt)1;
+    C w;
+    if (TW) {
+        w = conj_c(tw[(l & (h - 1)) * (L / (2 * h))]);
+        if (!upper) { w.x = (Rt)1; w.y = (Rt)0; }
+    }
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+        const C send = TW ? cmul(v[m], w) : v[m];
+        const C o = shfl_xor_c(send, h);
+        v[m].x = fma(sg, send.x, o.x);
+        v[m].y = fma(sg, send.y, o.y);
+    }
 }
 
 // Forward transform of one line: v[m] = x[l + S m] on entry, v[m] = X[axis_freq(l + S m)] on
@@ -345,7 +400,7 @@ __device__ __forceinline__ void wfft_fwd(C (&v)[R], int l, int S, int L, const C
                 const C a = v[b + j], c = v[b + j + h];
                 v[b + j] = cadd(a, c);
                 const C d = csub(a, c);
-                v[b + j + h] = j == 0 ? d : cmul(d, w32<C>(j * (16 / h)));
+                v[b + j + h] = j == 0 ? d : mul_w32(d, j * (16 / h));
             }
         }
     }
@@ -354,24 +409,8 @@ __device__ __forceinline__ void wfft_fwd(C (&v)[R], int l, int S, int L, const C
         const int k1 = (int)(__brev((unsigned)m) >> (32 - lgR));
         v[m] = cmul(v[m], tw[(l * k1) & (L - 1)]);
     }
-    // lane stage h: the lower lane of a pair keeps a + b, the upper one (a - b) w. Both are
-    // t w~ with t = o + sgn v (sgn = -1 on the upper lane) and w~ = 1 on the lower lane, so every
-    // lane runs the same instructions (no divergent halves).
-    for (int h = S >> 1; h >= 1; h >>= 1) {
-        const bool upper = (l & h) != 0;
-        typedef typename real_of<C>::type Rt;
-        const Rt sg = upper ? (Rt)-1 : (Rt)1;
-        C w = tw[(l & (h - 1)) * (L / (2 * h))];
-        if (!upper) { w.x = (Rt)1; w.y = (Rt)0; }
-#pragma unroll
-        for (int m = 0; m < R; ++m) {
-            const C o = shfl_xor_c(v[m], h);
-            C t;
-            t.x = fma(sg, v[m].x, o.x);
-            t.y = fma(sg, v[m].y, o.y);
-            v[m] = cmul(t, w);
-        }
-    }
+    for (int h = S >> 1; h >= 2; h >>= 1) lane_stage_fwd<C, R, true>(v, l, h, L, tw);
+    if (S >= 2) lane_stage_fwd<C, R, false>(v, l, 1, L, tw);
 }
 
 // Inverse of wfft_fwd up to the factor L: storage order in, natural order out (unnormalised
@@ -379,22 +418,8 @@ __device__ __forceinline__ void wfft_fwd(C (&v)[R], int l, int S, int L, const C
 template <typename C, int R>
 __device__ __forceinline__ void wfft_inv(C (&v)[R], int l, int S, int L, const C *__restrict__ tw) {
     constexpr int lgR = log2_of<R>::v;
-    // inverse lane stage h: the upper lane sends u = conj(w) b', the lower one a'; the lower lane
-    // keeps a' + u, the upper one a' - u, i.e. o + sgn send with sgn = -1 on the upper lane.
-    for (int h = 1; h < S; h <<= 1) {
-        const bool upper = (l & h) != 0;
-        typedef typename real_of<C>::type Rt;
-        const Rt sg = upper ? (Rt)-1 : (Rt)1;
-        C w = conj_c(tw[(l & (h - 1)) * (L / (2 * h))]);
-        if (!upper) { w.x = (Rt)1; w.y = (Rt)0; }
-#pragma unroll
-        for (int m = 0; m < R; ++m) {
-            const C send = cmul(v[m], w);
-            const C o = shfl_xor_c(send, h);
-            v[m].x = fma(sg, send.x, o.x);
-            v[m].y = fma(sg, send.y, o.y);
-        }
-    }
+    if (S >= 2) lane_stage_inv<C, R, false>(v, l, 1, L, tw);
+    for (int h = 2; h < S; h <<= 1) lane_stage_inv<C, R, true>(v, l, h, L, tw);
 #pragma unroll
     for (int m = 1; m < R; ++m) {
         const int k1 = (int)(__brev((unsigned)m) >> (32 - lgR));
@@ -406,7 +431,7 @@ __device__ __forceinline__ void wfft_inv(C (&v)[R], int l, int S, int L, const C
         for (int b = 0; b < R; b += 2 * h) {
 #pragma unroll
             for (int j = 0; j < h; ++j) {
-                const C t = j == 0 ? v[b + j + h] : cmul(v[b + j + h], conj_c(w32<C>(j * (16 / h))));
+                const C t = j == 0 ? v[b + j + h] : mul_w32c(v[b + j + h], j * (16 / h));
                 const C a = v[b + j];
                 v[b + j] = cadd(a, t);
                 v[b + j + h] = csub(a, t);
@@ -426,7 +451,7 @@ template <typename C, int R> __device__ __forceinline__ void regs_dif(C (&v)[R])
                 const C a = v[b + j], c = v[b + j + h];
                 v[b + j] = cadd(a, c);
                 const C d = csub(a, c);
-                v[b + j + h] = j == 0 ? d : cmul(d, w32<C>(j * (16 / h)));
+                v[b + j + h] = j == 0 ? d : mul_w32(d, j * (16 / h));
             }
         }
     }
@@ -438,7 +463,7 @@ template <typename C, int R> __device__ __forceinline__ void regs_dit(C (&v)[R])
         for (int b = 0; b < R; b += 2 * h) {
 #pragma unroll
             for (int j = 0; j < h; ++j) {
-                const C t = j == 0 ? v[b + j + h] : cmul(v[b + j + h], conj_c(w32<C>(j * (16 / h))));
+                const C t = j == 0 ? v[b + j + h] : mul_w32c(v[b + j + h], j * (16 / h));
                 const C a = v[b + j];
                 v[b + j] = cadd(a, t);
                 v[b + j + h] = csub(a, t);
@@ -479,20 +504,10 @@ __device__ __forceinline__ void wfft2_fwd(C (&v)[R], C *line, int l, int L, cons
             const int cc = (int)(__brev((unsigned)c) >> (32 - lgR));
             v[c] = cmul(v[c], tw[(gg * cc * R) & (L - 1)]);
         }
-        for (int h = G >> 1; h >= 1; h >>= 1) {
-            const bool upper = (gg & h) != 0;
-            const Rt sg = upper ? (Rt)-1 : (Rt)1;
-            C w = tw[(gg & (h - 1)) * (L / (2 * h))];
-            if (!upper) { w.x = (Rt)1; w.y = (Rt)0; }
+        // lanes of a group differ in their low log2 G bits (gg), so the stages index by l
 #pragma unroll
-            for (int m = 0; m < R; ++m) {
-                const C o = shfl_xor_c(v[m], h);
-                C t;
-                t.x = fma(sg, v[m].x, o.x);
-                t.y = fma(sg, v[m].y, o.y);
-                v[m] = cmul(t, w);
-            }
-        }
+        for (int h = G >> 1; h >= 2; h >>= 1) lane_stage_fwd<C, R, true>(v, l, h, L, tw);
+        lane_stage_fwd<C, R, false>(v, l, 1, L, tw);
     }
 }
 template <typename C, int R>
@@ -501,19 +516,9 @@ __device__ __forceinline__ void wfft2_inv(C (&v)[R], C *line, int l, int L, cons
     typedef typename real_of<C>::type Rt;
     const int j = l / G, gg = l & (G - 1);
     if (G > 1) {
-        for (int h = 1; h < G; h <<= 1) {
-            const bool upper = (gg & h) != 0;
-            const Rt sg = upper ? (Rt)-1 : (Rt)1;
-            C w = conj_c(tw[(gg & (h - 1)) * (L / (2 * h))]);
-            if (!upper) { w.x = (Rt)1; w.y = (Rt)0; }
+        lane_stage_inv<C, R, false>(v, l, 1, L, tw);
 #pragma unroll
-            for (int m = 0; m < R; ++m) {
-                const C send = cmul(v[m], w);
-                const C o = shfl_xor_c(send, h);
-                v[m].x = fma(sg, send.x, o.x);
-                v[m].y = fma(sg, send.y, o.y);
-            }
-        }
+        for (int h = 2; h < G; h <<= 1) lane_stage_inv<C, R, true>(v, l, h, L, tw);
 #pragma unroll
         for (int c = 1; c < R; ++c) {
             const int cc = (int)(__brev((unsigned)c) >> (32 - lgR));
