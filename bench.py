@@ -38,6 +38,7 @@ METRIC = "FFT-PFF voxel-updates/s"
 # read.sum + dram__bytes_write.sum averaged over the captured launches), keyed by (workload,
 # precision, kernel class). A class without a capture of its current code reports null.
 TRAFFIC = {}
+TRAFFIC_SOURCE = {}
 
 
 def workload_desc(name=WORKLOAD):
@@ -318,10 +319,12 @@ def kernel_breakdown(torch, stream, g, w, state, steps):
 
 
 def roofline_of(bd, precision, workload, hbm_peak, hbm_src, f64):
-    """Roofline of the dominant kernel class (largest time per increment in the replay)."""
-    # single kernel templates only: the projection pass is a subset of k_axis, the FP64 residual
-    # class of the FP32 path mixes x and column passes
-    cls = {k: v for k, v in bd["classes"].items() if k not in ("projection_pass", "fp64_residual")}
+    """Roofline of the dominant kernel: the one with the largest time per increment in the replay.
+    The library times the column pass per template (k_axis) and its projection instance on its
+    own; the projection instance stands for the column pass, since it is one kernel whose every
+    launch does the same work. The FP64 residual class of the FP32 path mixes x and column
+    passes and is not a candidate."""
+    cls = {k: v for k, v in bd["classes"].items() if k not in ("k_axis", "fp64_residual")}
     dom = max(cls, key=lambda k: cls[k]["ms_per_step"])
     c = cls[dom]
     traffic = TRAFFIC.get((workload, precision, dom))
@@ -338,7 +341,8 @@ def roofline_of(bd, precision, workload, hbm_peak, hbm_src, f64):
                 "peak_source": hbm_src,
                 "per_launch": "half-spectrum components read + written over nx/2+1 columns, plus the field words "
                               "of the fused prologue / epilogue"}
-    roof.update({"kernel": dom, "traffic": traffic, "algorithmic_bytes": c["bytes_per_launch"],
+    name = "k_axis<OpProj> (mechanics projection pass)" if dom == "projection_pass" else dom
+    roof.update({"kernel": name, "traffic": traffic, "traffic_source": TRAFFIC_SOURCE.get((workload, precision, dom)), "algorithmic_bytes": c["bytes_per_launch"],
                  "avg_launch_us": c["avg_launch_us"], "launches_per_step": c["launches_per_step"],
                  "share": c["share"],
                  "timing": "CUDA events around every launch on the library stream, the timed increments replayed "
@@ -602,12 +606,34 @@ def batched_leg(torch, ws, precision, warmup, steps, tol):
             ra[i].append(g.step(ws[i].dtau))
     torch.cuda.synchronize()
     t_alone = time.perf_counter() - t0
+    # the same RVEs stepped concurrently without batching: one host thread per RVE, each on its
+    # own stream with its own graph launches (the GPU overlaps their kernels)
+    for g, b in zip(gs, blobs):
+        g.load(b)
+    rc = [[] for _ in ws]
+
+    def solo(i):
+        for _ in range(steps):
+            rc[i].append(gs[i].step(ws[i].dtau))
+    th = [threading.Thread(target=solo, args=(i,)) for i in range(len(gs))]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    torch.cuda.synchronize()
+    t_conc = time.perf_counter() - t0
     same = all(same_result(a, b) for x, y in zip(ra, rb) for a, b in zip(x, y))
+    same_c = all(same_result(a, b) for x, y in zip(ra, rc) for a, b in zip(x, y))
     vu = sum((r["mech_iters"] + r["dmg_iters"]) * g.nvox for g, rs in zip(gs, rb) for r in rs)
     for g in gs:
         g.close()
     return {"value": vu / t_batch, "unit": "voxel-updates/s", "wall_s": t_batch, "clocks": clk,
             "one_by_one": {"value": vu / t_alone, "wall_s": t_alone}, "speedup": t_alone / t_batch,
+            "concurrent_unbatched": {"value": vu / t_conc, "wall_s": t_conc, "bit_identical": same_c,
+                                     "what": "one host thread and stream per RVE, graph launches, no batching"},
+            "speedup_vs_concurrent": t_conc / t_batch,
             "bit_identical_to_one_by_one": same, "rves": len(ws),
             "classes": {"x".join(map(str, k)): len(v) for k, v in sorted(classes.items())},
             "setup_s": setup_s, "increments_per_rve": steps, "warmup": warmup,

@@ -304,8 +304,9 @@ int rve_server_submit(rve_server s, long id, const rve_config *cfg, const rve_mi
 int rve_server_wait(rve_server s, rve_request_result *out, int max, double timeout_s, int *n_out);
 int rve_server_stats(rve_server s, int *peak_inflight, size_t *peak_bytes, long *pending);
 /* Lockstep batching of the requests of one size class (grid, precision; staggered solver without
- * the split) through a shared rve_batch_group: on (the default) or off (every request steps on its
- * own). Results are the same either way. Set it before submitting. */
+ * the split) through a shared rve_batch_group: on, or off (the default: every request steps on its
+ * own stream, concurrently with the others, with graph-launched solve loops). Results are the same
+ * either way. Set it before submitting. */
 int rve_server_set_batching(rve_server s, int on);
 /* Finishes every submitted request, then joins the workers. */
 int rve_server_destroy(rve_server s);

@@ -216,7 +216,7 @@ struct XiTab {
 };
 
 
-__device__ __forceinline__ double inv_sqrt(double v) { return 1.0 / sqrt(v); }
+__device__ __forceinline__ double inv_sqrt(double v) { return rsqrt(v); }
 __device__ __forceinline__ float inv_sqrt(float v) { return rsqrtf(v); }
 
 // Symmetric-strain Galerkin projection P^ = Gamma0(lambda0 = 0, mu0 = 1/2):

@@ -345,15 +345,15 @@ static inline cudaError_t axis_twiddles_init() {
 // Forward lane stage h over the R values of each lane: the lower lane of a pair keeps a + b, the
 // upper one (a - b) w. Both are t w~ with t = o + sgn v (sgn = -1 on the upper lane) and w~ = 1 on
 // the lower lane, so every lane runs the same instructions (no divergent halves). TW = false for
-// h = 1, whose twiddle is w_L^0 = 1 on both lanes.
+// h = 1, whose twiddle is w_L^0 = 1 on both lanes. tsh = log2(L / (2 h)) (the twiddle stride).
 template <typename C, int R, bool TW>
-__device__ __forceinline__ void lane_stage_fwd(C (&v)[R], int l, int h, int L, const C *__restrict__ tw) {
+__device__ __forceinline__ void lane_stage_fwd(C (&v)[R], int l, int h, int tsh, const C *__restrict__ tw) {
     typedef typename real_of<C>::type Rt;
     const bool upper = (l & h) != 0;
     const Rt sg = upper ? (Rt)-1 : (Rt)1;
     C w;
     if (TW) {
-        w = tw[(l & (h - 1)) * (L / (2 * h))];
+        w = tw[(l & (h - 1)) << tsh];
         if (!upper) { w.x = (Rt)1; w.y = (Rt)0; }
     }
 #pragma unroll
@@ -368,13 +368,13 @@ __device__ __forceinline__ void lane_stage_fwd(C (&v)[R], int l, int h, int L, c
 // Inverse lane stage h: the upper lane sends u = conj(w) b', the lower one a'; the lower lane keeps
 // a' + u, the upper one a' - u, i.e. o + sgn send with sgn = -1 on the upper lane.
 template <typename C, int R, bool TW>
-__device__ __forceinline__ void lane_stage_inv(C (&v)[R], int l, int h, int L, const C *__restrict__ tw) {
+__device__ __forceinline__ void lane_stage_inv(C (&v)[R], int l, int h, int tsh, const C *__restrict__ tw) {
     typedef typename real_of<C>::type Rt;
     const bool upper = (l & h) != 0;
     const Rt sg = upper ? (Rt)-1 : (Rt)1;
     C w;
     if (TW) {
-        w = conj_c(tw[(l & (h - 1)) * (L / (2 * h))]);
+        w = conj_c(tw[(l & (h - 1)) << tsh]);
         if (!upper) { w.x = (Rt)1; w.y = (Rt)0; }
     }
 #pragma unroll
@@ -409,8 +409,10 @@ __device__ __forceinline__ void wfft_fwd(C (&v)[R], int l, int S, int L, const C
         const int k1 = (int)(__brev((unsigned)m) >> (32 - lgR));
         v[m] = cmul(v[m], tw[(l * k1) & (L - 1)]);
     }
-    for (int h = S >> 1; h >= 2; h >>= 1) lane_stage_fwd<C, R, true>(v, l, h, L, tw);
-    if (S >= 2) lane_stage_fwd<C, R, false>(v, l, 1, L, tw);
+    const int lgL = ilog2(L);
+    int lgh = ilog2(S) - 1;
+    for (int h = S >> 1; h >= 2; h >>= 1, --lgh) lane_stage_fwd<C, R, true>(v, l, h, lgL - 1 - lgh, tw);
+    if (S >= 2) lane_stage_fwd<C, R, false>(v, l, 1, 0, tw);
 }
 
 // Inverse of wfft_fwd up to the factor L: storage order in, natural order out (unnormalised
@@ -418,8 +420,10 @@ __device__ __forceinline__ void wfft_fwd(C (&v)[R], int l, int S, int L, const C
 template <typename C, int R>
 __device__ __forceinline__ void wfft_inv(C (&v)[R], int l, int S, int L, const C *__restrict__ tw) {
     constexpr int lgR = log2_of<R>::v;
-    if (S >= 2) lane_stage_inv<C, R, false>(v, l, 1, L, tw);
-    for (int h = 2; h < S; h <<= 1) lane_stage_inv<C, R, true>(v, l, h, L, tw);
+    const int lgL = ilog2(L);
+    if (S >= 2) lane_stage_inv<C, R, false>(v, l, 1, 0, tw);
+    int lgh = 1;
+    for (int h = 2; h < S; h <<= 1, ++lgh) lane_stage_inv<C, R, true>(v, l, h, lgL - 1 - lgh, tw);
 #pragma unroll
     for (int m = 1; m < R; ++m) {
         const int k1 = (int)(__brev((unsigned)m) >> (32 - lgR));
@@ -506,8 +510,8 @@ __device__ __forceinline__ void wfft2_fwd(C (&v)[R], C *line, int l, int L, cons
         }
         // lanes of a group differ in their low log2 G bits (gg), so the stages index by l
 #pragma unroll
-        for (int h = G >> 1; h >= 2; h >>= 1) lane_stage_fwd<C, R, true>(v, l, h, L, tw);
-        lane_stage_fwd<C, R, false>(v, l, 1, L, tw);
+        for (int h = G >> 1; h >= 2; h >>= 1) lane_stage_fwd<C, R, true>(v, l, h, ilog2(L) - 1 - ilog2(h), tw);
+        lane_stage_fwd<C, R, false>(v, l, 1, 0, tw);
     }
 }
 template <typename C, int R>
@@ -516,9 +520,9 @@ __device__ __forceinline__ void wfft2_inv(C (&v)[R], C *line, int l, int L, cons
     typedef typename real_of<C>::type Rt;
     const int j = l / G, gg = l & (G - 1);
     if (G > 1) {
-        lane_stage_inv<C, R, false>(v, l, 1, L, tw);
+        lane_stage_inv<C, R, false>(v, l, 1, 0, tw);
 #pragma unroll
-        for (int h = 2; h < G; h <<= 1) lane_stage_inv<C, R, true>(v, l, h, L, tw);
+        for (int h = 2; h < G; h <<= 1) lane_stage_inv<C, R, true>(v, l, h, ilog2(L) - 1 - ilog2(h), tw);
 #pragma unroll
         for (int c = 1; c < R; ++c) {
             const int cc = (int)(__brev((unsigned)c) >> (32 - lgR));
@@ -556,12 +560,12 @@ template <typename C> __host__ __device__ constexpr int axis_line_stride(int L, 
 // groups of lines when there are more lines than warps. INV selects the inverse network.
 template <typename C, int R, bool INV>
 __device__ __forceinline__ void axis_lines(C *s, int nlines, int LS, int L, const C *__restrict__ tw) {
-    const int S = L / R;
-    const int lpw = 32 / S;  // lines per warp
+    const int lgS = ilog2(L) - log2_of<R>::v, S = 1 << lgS;
+    const int lpw = 32 >> lgS;  // lines per warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int l = lane & (S - 1);
     for (int grp = warp; grp * lpw < nlines; grp += nwarps) {  // uniform across the warp
-        const int line = grp * lpw + lane / S;
+        const int line = grp * lpw + (lane >> lgS);
         const bool valid = line < nlines;
         C *p = s + (size_t)(valid ? line : 0) * LS;
         C v[R];
@@ -604,8 +608,11 @@ __device__ __forceinline__ void axis_body(const Geom &g, int axis, int CW,
     const int LS = axis_line_stride<C>(L, CW);
     const int kx0 = blockIdx.x * CW;
     const int other = blockIdx.y;
-    const long long lstride = axis == 1 ? (long long)g.Px : (long long)g.Px * g.ny;
-    const long long base = axis == 1 ? (long long)other * g.ny * g.Px : (long long)other * g.Px;
+    // element offsets in 32 bits: every spectrum of a valid configuration (at most 2^24 voxels,
+    // x padded to Px <= max(16, nx/2 + 16)) has fewer than 2^29 elements over all its components
+    const unsigned Nh = (unsigned)g.Nh;
+    const unsigned lstride = axis == 1 ? (unsigned)g.Px : (unsigned)g.Px * g.ny;
+    const unsigned base = (axis == 1 ? (unsigned)other * g.ny * g.Px : (unsigned)other * g.Px) + kx0;
     const int nth = blockDim.x;
     const int npt = L * CW;  // points of one component in the tile
     // 1. coalesced load: i = (c, pos, cc), cc fastest. Each thread issues UB loads before it
@@ -622,7 +629,7 @@ __device__ __forceinline__ void axis_body(const Geom &g, int axis, int CW,
                 const int c = i >> (lgL + lgCW);
                 const int rem = i & (npt - 1);
                 const int pos = rem >> lgCW, cc = rem & (CW - 1);
-                tmp[u] = __ldg(spec_in + (size_t)c * g.Nh + base + pos * lstride + kx0 + cc);
+                tmp[u] = __ldg(spec_in + (c * Nh + base + pos * lstride + cc));
             }
         }
 #pragma unroll
@@ -632,7 +639,7 @@ __device__ __forceinline__ void axis_body(const Geom &g, int axis, int CW,
                 const int c = i >> (lgL + lgCW);
                 const int rem = i & (npt - 1);
                 const int pos = rem >> lgCW, cc = rem & (CW - 1);
-                s[(size_t)((c << lgCW) + cc) * LS + pos] = tmp[u];
+                s[((c << lgCW) + cc) * LS + pos] = tmp[u];
             }
         }
     }
@@ -649,10 +656,10 @@ __device__ __forceinline__ void axis_body(const Geom &g, int axis, int CW,
             const int kz = axis == 1 ? (g.nz > 1 ? other : 0) : kk;
             C in[NCI], out[NCO];
 #pragma unroll
-            for (int c = 0; c < NCI; ++c) in[c] = s[(size_t)((c << lgCW) + cc) * LS + p];
+            for (int c = 0; c < NCI; ++c) in[c] = s[((c << lgCW) + cc) * LS + p];
             op.apply(g, kx, ky, kz, in, out);
 #pragma unroll
-            for (int c = 0; c < NCO; ++c) s[(size_t)((c << lgCW) + cc) * LS + p] = out[c];
+            for (int c = 0; c < NCO; ++c) s[((c << lgCW) + cc) * LS + p] = out[c];
         }
         __syncthreads();
         axis_lines<C, R, true>(s, NCO * CW, LS, L, tw);
@@ -663,7 +670,7 @@ __device__ __forceinline__ void axis_body(const Geom &g, int axis, int CW,
         const int c = i >> (lgL + lgCW);
         const int rem = i & (npt - 1);
         const int pos = rem >> lgCW, cc = rem & (CW - 1);
-        spec_out[(size_t)c * g.Nh + base + pos * lstride + kx0 + cc] = s[(size_t)((c << lgCW) + cc) * LS + pos];
+        spec_out[c * Nh + base + pos * lstride + cc] = s[((c << lgCW) + cc) * LS + pos];
     }
 }
 

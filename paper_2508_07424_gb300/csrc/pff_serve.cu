@@ -55,7 +55,9 @@ struct Server {
     long submitted = 0, finished = 0;
     bool stop = false;
     int device = 0;
-    bool batching = true;
+    // off by default: requests stepping concurrently, each on its own stream with graph-launched
+    // solve loops, measured faster than lockstep batches of plain launches on every grid class
+    bool batching = false;
     // one lockstep group per size class: (dim, nx, ny, nz, precision)
     std::map<std::tuple<int, int, int, int, int>, rve_batch_group> groups;
     rve_batch_group group_for(const rve_config &c) {

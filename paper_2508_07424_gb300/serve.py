@@ -15,7 +15,7 @@ from .rve import make_micro, workload_config
 
 
 class Server:
-    def __init__(self, max_inflight=8, hbm_budget_bytes=64 << 30, batching=True):
+    def __init__(self, max_inflight=8, hbm_budget_bytes=64 << 30, batching=False):
         self.h = capi.rve_server()
         capi.check(capi.lib().rve_server_create(max_inflight, hbm_budget_bytes, C.byref(self.h)), "rve_server_create")
         capi.check(capi.lib().rve_server_set_batching(self.h, int(batching)), "rve_server_set_batching")

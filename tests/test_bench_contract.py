@@ -42,18 +42,25 @@ def test_both_arms_name_the_same_metric_and_config():
     assert d["config"] == bench.workload_config(bench.WORKLOAD, "fp64", "staggered", 1)
 
 
-def test_roofline_of_dominant_kernel_class():
+def test_roofline_of_dominant_kernel():
+    """The projection instance stands for the column-pass template; the largest candidate wins."""
     sys.path.insert(0, ROOT)
     import bench
     bd = {"classes": {
-        "k_axis": {"ms_per_step": 5.0, "bytes_per_launch": 4e6, "avg_launch_us": 10.0, "launches_per_step": 500,
+        "k_axis": {"ms_per_step": 12.0, "bytes_per_launch": 4e6, "avg_launch_us": 10.0, "launches_per_step": 500,
                    "share": 0.3, "GB_s": 400.0, "TFLOP_s": 0.5},
         "k_x_fwd": {"ms_per_step": 3.0, "bytes_per_launch": 5e6, "avg_launch_us": 6.0, "launches_per_step": 500,
                     "share": 0.2, "GB_s": 800.0, "TFLOP_s": 0.4},
         "projection_pass": {"ms_per_step": 9.0, "bytes_per_launch": 6e6, "avg_launch_us": 12.0,
-                            "launches_per_step": 100, "share": 0.1, "GB_s": 500.0, "TFLOP_s": 0.6}}}
+                            "launches_per_step": 100, "share": 0.1, "GB_s": 500.0, "TFLOP_s": 0.6},
+        "fp64_residual": {"ms_per_step": 20.0, "bytes_per_launch": 6e6, "avg_launch_us": 12.0,
+                          "launches_per_step": 100, "share": 0.1, "GB_s": 50.0, "TFLOP_s": 0.1}}}
     f64 = {"tflops": 1.0}
     r = bench.roofline_of(bd, "fp64", "w", 6000.0, "measured", f64)
-    assert r["kernel"] == "k_axis" and r["bound"] == "alu" and abs(r["frac"] - 0.5) < 1e-12
+    assert r["kernel"].startswith("k_axis<OpProj>") and r["bound"] == "alu" and abs(r["frac"] - 0.6) < 1e-12
+    assert r["avg_launch_us"] == 12.0 and r["algorithmic_bytes"] == 6e6
     r = bench.roofline_of(bd, "fp32r", "w", 6000.0, "measured", f64)
-    assert r["bound"] == "hbm" and abs(r["frac"] - 400.0 / 6000.0) < 1e-12 and r["traffic"] is None
+    assert r["bound"] == "hbm" and abs(r["frac"] - 500.0 / 6000.0) < 1e-12 and r["traffic"] is None
+    bd["classes"]["k_x_fwd"]["ms_per_step"] = 10.0
+    r = bench.roofline_of(bd, "fp32r", "w", 6000.0, "measured", f64)
+    assert r["kernel"] == "k_x_fwd" and abs(r["frac"] - 800.0 / 6000.0) < 1e-12
