@@ -674,6 +674,7 @@ inline void pinv_solve(int m, const double *Min, const double *b, double rcond, 
 // Column-tile table of the autotuner: process-wide, backed by a text cache file of lines
 // "<key> <cw_y> <cw_z>" (the last line for a key wins).
 // ------------------------------------------------------------------------------------------------
+constexpr int kColumnPassRev = 2;  // 16 points per lane on lines of 16-128 points
 inline std::mutex g_tile_mu;
 inline std::mutex g_tune_mu;  // one measurement at a time, so concurrent handles do not skew it
 inline std::map<std::string, std::pair<int, int>> g_tiles;
@@ -1081,8 +1082,10 @@ struct Engine : EngineBase {
         cudaDeviceProp pr;
         CK(cudaGetDeviceProperties(&pr, dev));
         char buf[512];
-        std::snprintf(buf, sizeof(buf), "%s|sm%d%d|d%d|%dx%dx%d|%s", pr.name, pr.major, pr.minor, D, g.nx, g.ny, g.nz,
-                      kSingle ? "fp32" : "fp64");
+        // kColumnPassRev names the column-pass code the timings were taken on: a cache written by
+        // another revision of it is not reused
+        std::snprintf(buf, sizeof(buf), "%s|sm%d%d|d%d|%dx%dx%d|%s|r%d", pr.name, pr.major, pr.minor, D, g.nx, g.ny,
+                      g.nz, kSingle ? "fp32" : "fp64", kColumnPassRev);
         std::string k(buf);
         for (char &ch : k)
             if (ch == ' ') ch = '_';

@@ -277,21 +277,25 @@ __global__ void __launch_bounds__(512) k_x_mid_b(Geom g, SlotArgs<Mid> args,
 template <int R> struct log2_of { static constexpr int v = R == 1 ? 0 : 1 + log2_of<R / 2>::v; };
 template <> struct log2_of<1> { static constexpr int v = 0; };
 
-// Points per lane of the warp transform of a line of L points (S = L / R lanes, S <= 32).
+// Points per lane of the warp transform of a line of L points (S = L / R lanes, S <= 32), and
+// whether the line takes the two-pass form (L >= 256, one line per warp) or the single-pass form
+// (a lane group of S lanes per line). Up to 128 points, 16 per lane keep most butterflies in
+// registers: a 128-point line has 3 lane stages instead of the 5 that 4 per lane would need.
 __host__ __device__ constexpr int axis_points_per_lane(int L) {
-    return L <= 128 ? 4 : (L == 256 ? 8 : (L == 512 ? 16 : 32));
+    return L < 16 ? 4 : (L <= 128 ? 16 : (L == 256 ? 8 : (L == 512 ? 16 : 32)));
 }
+__host__ __device__ constexpr bool axis_two_pass(int L) { return L >= 256; }
 __device__ __forceinline__ int brev_bits(int v, int bits) {
     return bits == 0 ? 0 : (int)(__brev((unsigned)v) >> (32 - bits));
 }
 __device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
 // Frequency index held at storage position p of a line of L points after the forward transform.
-// R < 8 (wfft_fwd): p = l + S m holds brev_R(m) + R brev_S(l). R >= 8 (wfft2_fwd, S = 32 lanes in
-// G = 32 / R groups): p = l + 32 c holds brev_R(l / G) + R brev_R(c) + R^2 brev_G(l mod G).
+// Single pass (wfft_fwd): p = l + S m holds brev_R(m) + R brev_S(l). Two-pass (wfft2_fwd, S = 32
+// lanes in G = 32 / R groups): p = l + 32 c holds brev_R(l / G) + R brev_R(c) + R^2 brev_G(l mod G).
 __device__ __forceinline__ int axis_freq(int p, int L) {
     const int R = axis_points_per_lane(L);
     const int lgR = ilog2(R), lgS = ilog2(L) - lgR;
-    if (R < 8) {
+    if (!axis_two_pass(L)) {
         const int m = p >> lgS, l = p & ((1 << lgS) - 1);
         return brev_bits(m, lgR) + (brev_bits(l, lgS) << lgR);
     }
@@ -553,12 +557,12 @@ template <typename C> __host__ __device__ constexpr int axis_line_pad(int CW) {
 // two-pass transform where it is used (R >= 8; 32 is a multiple of the bank period, so the
 // padding keeps its effect).
 template <typename C> __host__ __device__ constexpr int axis_line_stride(int L, int CW) {
-    return L + axis_line_pad<C>(CW) + (axis_points_per_lane(L) >= 8 ? 32 : 0);
+    return L + axis_line_pad<C>(CW) + (axis_two_pass(L) ? 32 : 0);
 }
 
 // Transform the lines [0, nlines) of the tile, one line per lane group of S lanes, looping over
 // groups of lines when there are more lines than warps. INV selects the inverse network.
-template <typename C, int R, bool INV>
+template <typename C, int R, bool TWO, bool INV>
 __device__ __forceinline__ void axis_lines(C *s, int nlines, int LS, int L, const C *__restrict__ tw) {
     const int lgS = ilog2(L) - log2_of<R>::v, S = 1 << lgS;
     const int lpw = 32 >> lgS;  // lines per warp
@@ -571,7 +575,7 @@ __device__ __forceinline__ void axis_lines(C *s, int nlines, int LS, int L, cons
         C v[R];
 #pragma unroll
         for (int m = 0; m < R; ++m) v[m] = p[l + S * m];
-        if constexpr (R >= 8) {  // S = 32: one line per warp, every lane of it valid or not
+        if constexpr (TWO) {  // S = 32: one line per warp, every lane of it valid or not
             if constexpr (INV) wfft2_inv<C, R>(v, p, l, L, tw);
             else wfft2_fwd<C, R>(v, p, l, L, tw);
         } else {
@@ -591,8 +595,17 @@ __device__ __forceinline__ void axis_lines(C *s, int nlines, int LS, int L, cons
 template <typename T> __host__ __device__ constexpr int axis_max_threads(int R) {
     return (R >= 16 || (sizeof(T) == 8 && R >= 8)) ? 256 : 512;
 }
+// Dispatch key of the column-pass instances: points per lane and form.
+enum { AXK_4 = 0, AXK_16 = 1, AXK_8T = 2, AXK_16T = 3, AXK_32T = 4 };
+__host__ __device__ constexpr int axis_form(int L) {
+    return axis_two_pass(L) ? (L == 256 ? AXK_8T : (L == 512 ? AXK_16T : AXK_32T)) : (L < 16 ? AXK_4 : AXK_16);
+}
+template <int K> struct axis_form_of {
+    static constexpr int R = K == AXK_4 ? 4 : (K == AXK_8T ? 8 : (K == AXK_32T ? 32 : 16));
+    static constexpr bool TWO = K >= AXK_8T;
+};
 
-template <typename T, int NCI, int NCO, int MODE, int R, class Op>
+template <typename T, int NCI, int NCO, int MODE, int K, class Op>
 __device__ __forceinline__ void axis_body(const Geom &g, int axis, int CW,
                                           const typename cplx_of<T>::type *__restrict__ spec_in,
                                           typename cplx_of<T>::type *spec_out, const Op &op,
@@ -645,7 +658,9 @@ __device__ __forceinline__ void axis_body(const Geom &g, int axis, int CW,
     }
     __syncthreads();
     // 2. transforms (and the operator between them)
-    axis_lines<C, R, MODE == AX_INV>(s, NCI * CW, LS, L, tw);
+    constexpr int R = axis_form_of<K>::R;
+    constexpr bool TWO = axis_form_of<K>::TWO;
+    axis_lines<C, R, TWO, MODE == AX_INV>(s, NCI * CW, LS, L, tw);
     if constexpr (MODE == AX_FWD_OP_INV) {
         __syncthreads();
         for (int i = threadIdx.x; i < npt; i += nth) {
@@ -662,7 +677,7 @@ __device__ __forceinline__ void axis_body(const Geom &g, int axis, int CW,
             for (int c = 0; c < NCO; ++c) s[((c << lgCW) + cc) * LS + p] = out[c];
         }
         __syncthreads();
-        axis_lines<C, R, true>(s, NCO * CW, LS, L, tw);
+        axis_lines<C, R, TWO, true>(s, NCO * CW, LS, L, tw);
     }
     __syncthreads();
     // 3. coalesced store
@@ -674,19 +689,19 @@ __device__ __forceinline__ void axis_body(const Geom &g, int axis, int CW,
     }
 }
 
-template <typename T, int NCI, int NCO, int MODE, int R, class Op>
-__global__ void __launch_bounds__(axis_max_threads<T>(R))
+template <typename T, int NCI, int NCO, int MODE, int K, class Op>
+__global__ void __launch_bounds__(axis_max_threads<T>(axis_form_of<K>::R))
     k_axis(Geom g, int axis, int CW, const typename cplx_of<T>::type *__restrict__ spec_in,
            typename cplx_of<T>::type *spec_out, Op op, const typename cplx_of<T>::type *__restrict__ tw, Scal *sc) {
-    axis_body<T, NCI, NCO, MODE, R>(g, axis, CW, spec_in, spec_out, op, tw, sc);
+    axis_body<T, NCI, NCO, MODE, K>(g, axis, CW, spec_in, spec_out, op, tw, sc);
 }
 
-template <typename T, int NCI, int NCO, int MODE, int R, class Op>
-__global__ void __launch_bounds__(axis_max_threads<T>(R))
+template <typename T, int NCI, int NCO, int MODE, int K, class Op>
+__global__ void __launch_bounds__(axis_max_threads<T>(axis_form_of<K>::R))
     k_axis_b(Geom g, int axis, int CW, SlotArgs<Op> args, const typename cplx_of<T>::type *__restrict__ tw) {
     typedef typename cplx_of<T>::type C;
     const SlotArg<Op> &a = args.a[blockIdx.z];
-    axis_body<T, NCI, NCO, MODE, R>(g, axis, CW, (const C *)a.spec, (C *)a.spec, a.f, tw, a.sc);
+    axis_body<T, NCI, NCO, MODE, K>(g, axis, CW, (const C *)a.spec, (C *)a.spec, a.f, tw, a.sc);
 }
 
 
@@ -711,22 +726,24 @@ using axis_kernel_t = void (*)(Geom, int, int, const typename cplx_of<T>::type *
 
 // The instance of k_axis for the points per lane of an axis of L points.
 template <typename T, int NCI, int NCO, int MODE, class Op> inline axis_kernel_t<T, Op> axis_kernel(int L) {
-    switch (axis_points_per_lane(L)) {
-    case 4: return k_axis<T, NCI, NCO, MODE, 4, Op>;
-    case 8: return k_axis<T, NCI, NCO, MODE, 8, Op>;
-    case 16: return k_axis<T, NCI, NCO, MODE, 16, Op>;
-    default: return k_axis<T, NCI, NCO, MODE, 32, Op>;
+    switch (axis_form(L)) {
+    case AXK_4: return k_axis<T, NCI, NCO, MODE, AXK_4, Op>;
+    case AXK_16: return k_axis<T, NCI, NCO, MODE, AXK_16, Op>;
+    case AXK_8T: return k_axis<T, NCI, NCO, MODE, AXK_8T, Op>;
+    case AXK_16T: return k_axis<T, NCI, NCO, MODE, AXK_16T, Op>;
+    default: return k_axis<T, NCI, NCO, MODE, AXK_32T, Op>;
     }
 }
 
 template <typename T, class Op>
 using axis_kernel_b_t = void (*)(Geom, int, int, SlotArgs<Op>, const typename cplx_of<T>::type *__restrict__);
 template <typename T, int NCI, int NCO, int MODE, class Op> inline axis_kernel_b_t<T, Op> axis_kernel_b(int L) {
-    switch (axis_points_per_lane(L)) {
-    case 4: return k_axis_b<T, NCI, NCO, MODE, 4, Op>;
-    case 8: return k_axis_b<T, NCI, NCO, MODE, 8, Op>;
-    case 16: return k_axis_b<T, NCI, NCO, MODE, 16, Op>;
-    default: return k_axis_b<T, NCI, NCO, MODE, 32, Op>;
+    switch (axis_form(L)) {
+    case AXK_4: return k_axis_b<T, NCI, NCO, MODE, AXK_4, Op>;
+    case AXK_16: return k_axis_b<T, NCI, NCO, MODE, AXK_16, Op>;
+    case AXK_8T: return k_axis_b<T, NCI, NCO, MODE, AXK_8T, Op>;
+    case AXK_16T: return k_axis_b<T, NCI, NCO, MODE, AXK_16T, Op>;
+    default: return k_axis_b<T, NCI, NCO, MODE, AXK_32T, Op>;
     }
 }
 
