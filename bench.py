@@ -37,8 +37,18 @@ METRIC = "FFT-PFF voxel-updates/s"
 # DRAM bytes per launch of a kernel class, from ncu captures of this build's kernels (dram__bytes_
 # read.sum + dram__bytes_write.sum averaged over the captured launches), keyed by (workload,
 # precision, kernel class). A class without a capture of its current code reports null.
-TRAFFIC = {}
-TRAFFIC_SOURCE = {}
+TRAFFIC = {
+    ("fibre_composite_512", "fp64", "projection_pass"): 6432256 + 0,
+    ("polycrystal_3d_128", "fp32r", "projection_pass"): 56673536 + 2820608,
+}
+TRAFFIC_SOURCE = {
+    ("fibre_composite_512", "fp64", "projection_pass"):
+        "ncu --set full, one launch of k_axis<double,3,3,FWD_OP_INV,OpProj> in `bench.py --steps 1 --warmup 3` "
+        "(cold caches: the read half comes from DRAM, the writes stay in L2)",
+    ("polycrystal_3d_128", "fp32r", "projection_pass"):
+        "ncu --set full, one launch of k_axis<float,6,6,FWD_OP_INV,OpProj> in "
+        "`bench.py --workload polycrystal_3d_128 --precision fp32r --steps 1 --warmup 3` (cold caches)",
+}
 
 
 def workload_desc(name=WORKLOAD):
