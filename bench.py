@@ -279,7 +279,7 @@ def fp64_peak(torch, stream):
             "8 independent FMA chains per thread, CUDA events; best of 3 launches of ~1.5 s"}
 
 
-KERNEL_CLASSES = ("k_axis", "k_x_fwd", "k_x_inv", "k_x_mid", "k_pointwise", "fp64_residual")
+KERNEL_CLASSES = ("k_axis", "k_x_fwd", "k_x_inv", "k_x_mid", "k_pointwise", "fp64_residual", "cg_x_fwd", "cg_x_inv")
 
 
 def same_result(a, b):
@@ -330,11 +330,15 @@ def kernel_breakdown(torch, stream, g, w, state, steps):
 
 def roofline_of(bd, precision, workload, hbm_peak, hbm_src, f64):
     """Roofline of the dominant kernel: the one with the largest time per increment in the replay.
-    The library times the column pass per template (k_axis) and its projection instance on its
-    own; the projection instance stands for the column pass, since it is one kernel whose every
-    launch does the same work. The FP64 residual class of the FP32 path mixes x and column
-    passes and is not a candidate."""
-    cls = {k: v for k, v in bd["classes"].items() if k not in ("k_axis", "fp64_residual")}
+    The library times each kernel template as a class (k_axis, k_x_fwd, k_x_inv, ...) and, on
+    their own, three single kernels whose every launch does the same work: the mechanics
+    projection pass (inside k_axis) and the two x passes of the equilibrium CG iteration (inside
+    k_x_fwd / k_x_inv). Those stand for their templates; the FP64 residual class of the FP32 path
+    mixes x and column passes and is not a candidate."""
+    single = {"projection_pass": "k_axis", "cg_x_fwd": "k_x_fwd", "cg_x_inv": "k_x_inv"}
+    have = bd["classes"]
+    drop = {"fp64_residual"} | {tmpl for sub, tmpl in single.items() if sub in have}
+    cls = {k: v for k, v in have.items() if k not in drop}
     dom = max(cls, key=lambda k: cls[k]["ms_per_step"])
     c = cls[dom]
     traffic = TRAFFIC.get((workload, precision, dom))
@@ -351,7 +355,9 @@ def roofline_of(bd, precision, workload, hbm_peak, hbm_src, f64):
                 "peak_source": hbm_src,
                 "per_launch": "half-spectrum components read + written over nx/2+1 columns, plus the field words "
                               "of the fused prologue / epilogue"}
-    name = "k_axis<OpProj> (mechanics projection pass)" if dom == "projection_pass" else dom
+    name = {"projection_pass": "k_axis<OpProj> (mechanics projection pass)",
+            "cg_x_fwd": "k_x_fwd<ProCGCG> (forward x pass of the equilibrium CG)",
+            "cg_x_inv": "k_x_inv<EpiCGCG> (inverse x pass of the equilibrium CG)"}.get(dom, dom)
     roof.update({"kernel": name, "traffic": traffic, "traffic_source": TRAFFIC_SOURCE.get((workload, precision, dom)), "algorithmic_bytes": c["bytes_per_launch"],
                  "avg_launch_us": c["avg_launch_us"], "launches_per_step": c["launches_per_step"],
                  "share": c["share"],

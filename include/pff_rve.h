@@ -243,7 +243,9 @@ int rve_load(rve_handle h, const void *buf, size_t len);
  *   1 = every column pass (k_axis: projection, damage gradient / divergence / preconditioner),
  *   2 = k_x_fwd, 3 = k_x_inv, 4 = k_x_mid (the x-axis passes with their fused pointwise work),
  *   5 = k_pointwise, 6 = all launches, 7 = the FP64 residual passes of the FP32 path's
- *   equilibrium refinement (x and column passes in FP64; not counted in kinds 0-3).
+ *   equilibrium refinement (x and column passes in FP64; not counted in kinds 0-3),
+ *   8 / 9 = the forward / inverse x pass of the equilibrium CG iteration (single kernels,
+ *   k_x_fwd with the direction-update prologue and k_x_inv with the CG epilogue; inside 2 / 3).
  * total_ms: summed event time; launches: count; bytes_per_launch: average algorithmic bytes
  * (half-spectrum components read and written over the nx/2 + 1 columns, plus the field words
  * the fused prologue / epilogue reads and writes per voxel); flops_per_launch: average FFT flops

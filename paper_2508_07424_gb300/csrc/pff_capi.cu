@@ -359,7 +359,7 @@ int rve_timing_get(rve_handle h, int kind, double *total_ms, long *launches, dou
 
 int rve_timing_get_flops(rve_handle h, int kind, double *total_ms, long *launches, double *bytes_per_launch,
                          double *flops_per_launch) {
-    if (!h || kind < 0 || kind > 7) return RVE_EINVAL;
+    if (!h || kind < 0 || kind > 9) return RVE_EINVAL;
     GUARD_BEGIN
     double ms = 0.0, b = 0.0, f = 0.0;
     long n = 0;

@@ -732,6 +732,12 @@ inline void tile_store(const std::string &key, int y, int z) {
     std::fclose(f);
 }
 
+// The x passes of the equilibrium CG iteration, timed on their own (timing kinds 8, 9).
+template <class P> struct is_cg_dir : std::false_type {};
+template <typename U, int NSx> struct is_cg_dir<pff::ProCGCG<U, NSx>> : std::true_type {};
+template <class P> struct is_cg_epi : std::false_type {};
+template <typename U, int NSx> struct is_cg_epi<pff::EpiCGCG<U, NSx>> : std::true_type {};
+
 // ------------------------------------------------------------------------------------------------
 // The engine
 // ------------------------------------------------------------------------------------------------
@@ -803,7 +809,9 @@ struct Engine : EngineBase {
     size_t ev_used = 0;
     // per launch: kernel class (1 k_axis, 2 k_x_fwd, 3 k_x_inv, 4 k_x_mid, 5 k_pointwise), mechanics
     // projection pass?, algorithmic bytes and FFT flops
-    struct EvMeta { int kind; int proj; double bytes, flops; };
+    // sub: 1 = the mechanics projection pass, 2 / 3 = the forward / inverse x pass of the
+    // equilibrium CG iteration (single kernels inside kinds 1, 2, 3; reported as kinds 0, 8, 9)
+    struct EvMeta { int kind; int sub; double bytes, flops; };
     std::vector<EvMeta> ev_meta;
     double bytes_mech_axis = 0.0;
     std::map<const void *, size_t> smem_set;
@@ -1161,7 +1169,7 @@ struct Engine : EngineBase {
         }
     }
     // Events around one launch while timing is on (returns the end event to record after it).
-    cudaEvent_t tbeg(int kind, int proj, double bytes, double flops) {
+    cudaEvent_t tbeg(int kind, int sub, double bytes, double flops) {
         if (!timing) return nullptr;
         if (ev_used == ev_pool.size()) {
             cudaEvent_t a, b;
@@ -1169,7 +1177,7 @@ struct Engine : EngineBase {
             ev_pool.push_back({a, b});
         }
         if (ev_meta.size() < ev_pool.size()) ev_meta.resize(ev_pool.size());
-        ev_meta[ev_used] = EvMeta{kind, proj, bytes, flops};
+        ev_meta[ev_used] = EvMeta{kind, sub, bytes, flops};
         CK(cudaEventRecord(ev_pool[ev_used].first, st));
         return ev_pool[ev_used++].second;
     }
@@ -1244,7 +1252,8 @@ struct Engine : EngineBase {
         int th, bl; size_t sm; xcfg<U>(th, bl, sm);
         auto k = k_x_fwd<U, NC, Pro>;
         prep_smem(k, sm * NC);
-        cudaEvent_t e = tbeg(std::is_same<U, T>::value ? 2 : 7, 0, xbytes<U>(NC, rw_words<Pro>()), xflops(NC));
+        cudaEvent_t e = tbeg(std::is_same<U, T>::value ? 2 : 7, is_cg_dir<Pro>::value ? 2 : 0,
+                             xbytes<U>(NC, rw_words<Pro>()), xflops(NC));
         k<<<bl, th, sm * NC, st>>>(g, pro, spec_of<U>(), tw_of<U>(g.nx), partials, s);
         CK(cudaGetLastError());
         tend(e);
@@ -1254,7 +1263,8 @@ struct Engine : EngineBase {
         int th, bl; size_t sm; xcfg<U>(th, bl, sm);
         auto k = k_x_inv<U, NC, Epi>;
         prep_smem(k, sm * NC);
-        cudaEvent_t e = tbeg(std::is_same<U, T>::value ? 3 : 7, 0, xbytes<U>(NC, rw_words<Epi>()), xflops(NC));
+        cudaEvent_t e = tbeg(std::is_same<U, T>::value ? 3 : 7, is_cg_epi<Epi>::value ? 3 : 0,
+                             xbytes<U>(NC, rw_words<Epi>()), xflops(NC));
         k<<<bl, th, sm * NC, st>>>(g, spec_of<U>(), epi, tw_of<U>(g.nx), partials, s);
         CK(cudaGetLastError());
         tend(e);
@@ -2645,7 +2655,11 @@ struct Engine : EngineBase {
         long cnt = 0;
         for (size_t i = 0; i < ev_used; ++i) {
             const EvMeta &m = ev_meta[i];
-            const bool take = kind == 0 ? m.proj != 0 : kind == 6 ? true : m.kind == kind;  // 7: FP64 residual passes
+            const bool take = kind == 0   ? m.sub == 1
+                              : kind == 8 ? m.sub == 2
+                              : kind == 9 ? m.sub == 3
+                              : kind == 6 ? true
+                                          : m.kind == kind;  // 7: FP64 residual passes
             if (!take) continue;
             float t = 0.f;
             CK(cudaEventElapsedTime(&t, ev_pool[i].first, ev_pool[i].second));

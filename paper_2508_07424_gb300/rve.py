@@ -155,7 +155,7 @@ class Rve:
         launch, FFT flops per launch)}."""
         out = {}
         for kind, name in ((0, "projection_pass"), (1, "k_axis"), (2, "k_x_fwd"), (3, "k_x_inv"), (4, "k_x_mid"),
-                           (5, "k_pointwise"), (6, "all"), (7, "fp64_residual")):
+                           (5, "k_pointwise"), (6, "all"), (7, "fp64_residual"), (8, "cg_x_fwd"), (9, "cg_x_inv")):
             ms, n, b, f = C.c_double(), C.c_long(), C.c_double(), C.c_double()
             capi.check(capi.lib().rve_timing_get_flops(self.h, kind, C.byref(ms), C.byref(n), C.byref(b), C.byref(f)),
                        "rve_timing_get_flops")

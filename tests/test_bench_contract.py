@@ -64,3 +64,8 @@ def test_roofline_of_dominant_kernel():
     bd["classes"]["k_x_fwd"]["ms_per_step"] = 10.0
     r = bench.roofline_of(bd, "fp32r", "w", 6000.0, "measured", f64)
     assert r["kernel"] == "k_x_fwd" and abs(r["frac"] - 800.0 / 6000.0) < 1e-12
+    # the CG x pass stands for its template once the library times it on its own
+    bd["classes"]["cg_x_fwd"] = {"ms_per_step": 9.5, "bytes_per_launch": 9e6, "avg_launch_us": 8.0,
+                                 "launches_per_step": 400, "share": 0.2, "GB_s": 1125.0, "TFLOP_s": 0.3}
+    r = bench.roofline_of(bd, "fp32r", "w", 6000.0, "measured", f64)
+    assert r["kernel"].startswith("k_x_fwd<ProCGCG>") and abs(r["frac"] - 1125.0 / 6000.0) < 1e-12
