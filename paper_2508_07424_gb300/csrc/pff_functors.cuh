@@ -382,28 +382,17 @@ struct ProCGCG : MechBase<T, NS> {
     const Scal *scr;
     __device__ void eval(long long v, T *out, double *) const {
         const T al = (T)scr->alpha, be = (T)scr->beta;
-        // every load first, then the arithmetic and the stores: the loads of all components are
-        // in flight together instead of waiting behind the stores of the previous component
-        T rv[NS], pv[NS], wv[NS], sv[NS], xv[NS];
-#pragma unroll
-        for (int a = 0; a < NS; ++a) {
-            const size_t i = a * this->N + v;
-            rv[a] = ldro(r + i);
-            pv[a] = ldro(p + i);
-            wv[a] = ldro(w + i);
-            sv[a] = ldro(s + i);
-            xv[a] = ldro(x + i);
-        }
         T rn[NS];
 #pragma unroll
         for (int a = 0; a < NS; ++a) {
             const size_t i = a * this->N + v;
-            const T pi = rv[a] + be * pv[a];
-            const T si = wv[a] + be * sv[a];
+            const T ri = ldro(r + i);
+            const T pi = ri + be * ldro(p + i);
+            const T si = ldro(w + i) + be * ldro(s + i);
             p[i] = pi;
             s[i] = si;
-            x[i] = xv[a] + al * pi;
-            rn[a] = rv[a] - al * si;
+            x[i] = ldro(x + i) + al * pi;
+            rn[a] = ri - al * si;
             r[i] = rn[a];
         }
         this->stress(v, rn, out);
@@ -420,32 +409,26 @@ struct EpiCGCG {
     T *w;
     const T *r;
     long long N;
+    // FP32 path (see x_inv_body): per-thread partial sums in FP32, over the thread's voxels
+    static constexpr bool FACC = true;
+    __device__ void apply_f(long long v, const T *val, float *acc) const {
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+            const size_t i = a * N + v;
+            w[i] = val[a];
+            const float rv = (float)ldro(r + i);
+            acc[0] = fmaf(rv, rv, acc[0]);
+            acc[1] = fmaf((float)val[a], rv, acc[1]);
+        }
+    }
     __device__ void apply(long long v, const T *val, double *acc) const {
-        if constexpr (sizeof(T) == 4) {
-            // FP32 path: the components of one voxel are summed in FP32 and only the voxel sums
-            // are accumulated in FP64. FP64 issues at 1/64 of the FP32 rate on this part, and an
-            // FP64 product per component made the 6-component 3D epilogue FP64-bound.
-            float rv[NS];
 #pragma unroll
-            for (int a = 0; a < NS; ++a) rv[a] = ldro(r + a * N + v);
-            float gr = 0.f, dr = 0.f;
-#pragma unroll
-            for (int a = 0; a < NS; ++a) {
-                w[a * N + v] = val[a];
-                gr = fmaf(rv[a], rv[a], gr);
-                dr = fmaf(val[a], rv[a], dr);
-            }
-            acc[0] += (double)gr;
-            acc[1] += (double)dr;
-        } else {
-#pragma unroll
-            for (int a = 0; a < NS; ++a) {
-                const size_t i = a * N + v;
-                w[i] = val[a];
-                const double rv = (double)ldro(r + i);
-                acc[0] += rv * rv;
-                acc[1] += (double)val[a] * rv;
-            }
+        for (int a = 0; a < NS; ++a) {
+            const size_t i = a * N + v;
+            w[i] = val[a];
+            const double rv = (double)ldro(r + i);
+            acc[0] += rv * rv;
+            acc[1] += (double)val[a] * rv;
         }
     }
     struct Fin {
@@ -839,6 +822,18 @@ struct EpiPCGCG {
         acc[0] += rv * (double)uv;
         acc[1] += (double)wv * (double)uv;
         acc[2] += rv * rv;
+    }
+    // FP32 path (see x_inv_body): per-thread partial sums in FP32, over the thread's voxels
+    static constexpr bool FACC = true;
+    __device__ void apply_f(long long v, const T *val, float *acc) const {
+        const T a = ldro(acoef + ldro(gid + v)) + (hmul != (T)0 ? hmul * ldro(H + v) : (T)0);
+        const T uv = ldro(u + v);
+        const T wv = a * uv - val[0];
+        const float rv = (float)ldro(r + v);
+        w[v] = wv;
+        acc[0] = fmaf(rv, (float)uv, acc[0]);
+        acc[1] = fmaf((float)wv, (float)uv, acc[1]);
+        acc[2] = fmaf(rv, rv, acc[2]);
     }
     struct Fin {
         Scal *sc;

@@ -15,11 +15,18 @@
 // so a whole CG iteration is launched without host synchronisation.
 #pragma once
 
+#include <type_traits>
+
 #include "pff_common.cuh"
 
 namespace pff {
 
 enum { AX_FWD = 0, AX_INV = 1, AX_FWD_OP_INV = 2 };
+
+// Epilogues that define FACC = true also provide apply_f(v, val, float *acc), used on the FP32
+// path to accumulate a thread's partial sums in FP32.
+template <class E, class = void> struct facc_of : std::false_type {};
+template <class E> struct facc_of<E, std::void_t<decltype(E::FACC)>> : std::integral_constant<bool, E::FACC> {};
 
 // ---- x-axis forward (r2c) pass ------------------------------------------------------------------
 template <typename T, int NC, class Pro>
@@ -148,10 +155,18 @@ __device__ __forceinline__ void x_inv_body(const Geom &g, const typename cplx_of
     for (int c = 0; c < NC; ++c) load_packed<T, C>(g, spec, c, z, y0, line + c * nx, t, TL);
     __syncthreads();
     fft_lines<C, NC>(s, nx, g.lx, NC, NC, 1, tw, true);
-    double acc[Epi::NR > 0 ? Epi::NR : 1];
+    constexpr int NR1 = Epi::NR > 0 ? Epi::NR : 1;
+    double acc[NR1];
 #pragma unroll
-    for (int k = 0; k < (Epi::NR > 0 ? Epi::NR : 1); ++k) acc[k] = 0.0;
+    for (int k = 0; k < NR1; ++k) acc[k] = 0.0;
     const T sN = (T)g.invN;
+    // FP32 path with an epilogue that supports it: the thread's 8 voxels are summed in FP32 and
+    // converted once (FP64 issues at 1/64 of the FP32 rate on this part); the reduction across
+    // threads and CTAs stays FP64
+    constexpr bool F32ACC = sizeof(T) == 4 && facc_of<Epi>::value;
+    float accf[NR1];
+#pragma unroll
+    for (int k = 0; k < NR1; ++k) accf[k] = 0.f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int x = t + q * TL;
@@ -162,8 +177,17 @@ __device__ __forceinline__ void x_inv_body(const Geom &g, const typename cplx_of
             va[c] = v.x * sN;
             vb[c] = v.y * sN;
         }
-        epi.apply(row0 + x, va, acc);
-        epi.apply(row0 + nx + x, vb, acc);
+        if constexpr (F32ACC) {
+            epi.apply_f(row0 + x, va, accf);
+            epi.apply_f(row0 + nx + x, vb, accf);
+        } else {
+            epi.apply(row0 + x, va, acc);
+            epi.apply(row0 + nx + x, vb, acc);
+        }
+    }
+    if constexpr (F32ACC) {
+#pragma unroll
+        for (int k = 0; k < NR1; ++k) acc[k] = (double)accf[k];
     }
     if constexpr (Epi::NR > 0) reduce_finalize<Epi::NR>(acc, partials, sc, epi.fin(sc));
 }
