@@ -28,6 +28,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <string>
 #include <tuple>
 #include <type_traits>
@@ -815,6 +816,7 @@ struct Engine : EngineBase {
     std::vector<EvMeta> ev_meta;
     double bytes_mech_axis = 0.0;
     std::map<const void *, size_t> smem_set;
+    std::set<const void *> carveout_set;
     // CUDA graphs of one iteration chunk, keyed by (solver kind, solution buffer, coefficient
     // pointer): the kernels of a chunk take only pointers and the device scalar block, so one
     // captured graph is replayed for every chunk of every later solve of the same kind.
@@ -1159,6 +1161,21 @@ struct Engine : EngineBase {
         g_last_error = what;
         return code;
     }
+    // x passes of the FP32 path: the shared-memory carveout at its maximum, so that shared memory
+    // does not cap the resident CTAs below what their register bound allows (L1 caching does not
+    // help these streaming passes)
+    template <typename K> void prep_x(K kernel, size_t bytes) {
+        prep_smem(kernel, bytes);
+        if (sizeof(T) != 4 || carveout_set.count((const void *)kernel)) return;
+        // not while the stream is being captured into a graph: the attribute is set at the
+        // kernel's first launch outside a capture and applies to every later launch
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        CK(cudaStreamIsCapturing(st, &cs));
+        if (cs != cudaStreamCaptureStatusNone) return;
+        CK(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared));
+        carveout_set.insert((const void *)kernel);
+    }
     template <typename K> void prep_smem(K kernel, size_t bytes) {
         const void *key = (const void *)kernel;
         auto it = smem_set.find(key);
@@ -1251,7 +1268,7 @@ struct Engine : EngineBase {
     template <int NC, class Pro, typename U = T> void x_fwd(const Pro &pro, Scal *s) {
         int th, bl; size_t sm; xcfg<U>(th, bl, sm);
         auto k = k_x_fwd<U, NC, Pro>;
-        prep_smem(k, sm * NC);
+        prep_x(k, sm * NC);
         cudaEvent_t e = tbeg(std::is_same<U, T>::value ? 2 : 7, is_cg_dir<Pro>::value ? 2 : 0,
                              xbytes<U>(NC, rw_words<Pro>()), xflops(NC));
         k<<<bl, th, sm * NC, st>>>(g, pro, spec_of<U>(), tw_of<U>(g.nx), partials, s);
@@ -1262,7 +1279,7 @@ struct Engine : EngineBase {
     template <int NC, class Epi, typename U = T> void x_inv(const Epi &epi, Scal *s) {
         int th, bl; size_t sm; xcfg<U>(th, bl, sm);
         auto k = k_x_inv<U, NC, Epi>;
-        prep_smem(k, sm * NC);
+        prep_x(k, sm * NC);
         cudaEvent_t e = tbeg(std::is_same<U, T>::value ? 3 : 7, is_cg_epi<Epi>::value ? 3 : 0,
                              xbytes<U>(NC, rw_words<Epi>()), xflops(NC));
         k<<<bl, th, sm * NC, st>>>(g, spec_of<U>(), epi, tw_of<U>(g.nx), partials, s);
@@ -1274,7 +1291,7 @@ struct Engine : EngineBase {
     template <int NCI, int NCO, class Mid> void x_mid2(const Mid &mid, Scal *s) {
         int th, bl; size_t sm; xcfg(th, bl, sm);
         auto k = k_x_mid<T, NCI, NCO, Mid>;
-        prep_smem(k, sm * NCI);
+        prep_x(k, sm * NCI);
         cudaEvent_t e = tbeg(4, 0, xbytes(NCI + NCO, rw_words<Mid>()), xflops(NCI + NCO));
         k<<<bl, th, sm * NCI, st>>>(g, spec, mid, tw[g.nx], s);
         CK(cudaGetLastError());
@@ -1375,7 +1392,7 @@ struct Engine : EngineBase {
                  cudaStream_t s) {
         int th, bl; size_t sm; xcfg(th, bl, sm);
         auto k = k_x_fwd_b<T, NC, Pro>;
-        prep_smem(k, sm * NC);
+        prep_x(k, sm * NC);
         k<<<dim3(bl, 1, (unsigned)es.size()), th, sm * NC, s>>>(g, slot_args(es, fs, scs), tw[g.nx]);
     }
     template <int NC, class Epi>
@@ -1383,7 +1400,7 @@ struct Engine : EngineBase {
                  cudaStream_t s) {
         int th, bl; size_t sm; xcfg(th, bl, sm);
         auto k = k_x_inv_b<T, NC, Epi>;
-        prep_smem(k, sm * NC);
+        prep_x(k, sm * NC);
         k<<<dim3(bl, 1, (unsigned)es.size()), th, sm * NC, s>>>(g, slot_args(es, fs, scs), tw[g.nx]);
     }
     template <int NCI, int NCO, class Mid>
@@ -1391,7 +1408,7 @@ struct Engine : EngineBase {
                  cudaStream_t s) {
         int th, bl; size_t sm; xcfg(th, bl, sm);
         auto k = k_x_mid_b<T, NCI, NCO, Mid>;
-        prep_smem(k, sm * NCI);
+        prep_x(k, sm * NCI);
         k<<<dim3(bl, 1, (unsigned)es.size()), th, sm * NCI, s>>>(g, slot_args(es, fs, scs), tw[g.nx]);
     }
     template <int NCI, int NCO, int MODE, class Op>

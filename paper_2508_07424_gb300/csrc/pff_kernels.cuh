@@ -28,6 +28,12 @@ enum { AX_FWD = 0, AX_INV = 1, AX_FWD_OP_INV = 2 };
 template <class E, class = void> struct facc_of : std::false_type {};
 template <class E> struct facc_of<E, std::void_t<decltype(E::FACC)>> : std::integral_constant<bool, E::FACC> {};
 
+// Launch bounds of the x passes: at most 256 threads (max(128, nx / 4)); on the FP32 path at
+// least 3 such CTAs per SM (<= 85 registers), so that more warps cover the latency of the fused
+// pointwise loads, which bound the FP32 x passes of large grids.
+template <typename T> __host__ __device__ constexpr int x_max_threads() { return sizeof(T) == 4 ? 256 : 512; }
+template <typename T> __host__ __device__ constexpr int x_min_blocks() { return sizeof(T) == 4 ? 3 : 1; }
+
 // ---- x-axis forward (r2c) pass ------------------------------------------------------------------
 template <typename T, int NC, class Pro>
 __device__ __forceinline__ void x_fwd_body(const Geom &g, const Pro &pro, typename cplx_of<T>::type *__restrict__ spec,
@@ -79,7 +85,7 @@ __device__ __forceinline__ void x_fwd_body(const Geom &g, const Pro &pro, typena
 }
 
 template <typename T, int NC, class Pro>
-__global__ void __launch_bounds__(512) k_x_fwd(Geom g, Pro pro, typename cplx_of<T>::type *__restrict__ spec,
+__global__ void __launch_bounds__(x_max_threads<T>(), x_min_blocks<T>()) k_x_fwd(Geom g, Pro pro, typename cplx_of<T>::type *__restrict__ spec,
                                                const typename cplx_of<T>::type *__restrict__ tw, double *partials,
                                                Scal *sc) {
     x_fwd_body<T, NC>(g, pro, spec, tw, partials, sc);
@@ -100,7 +106,7 @@ template <class F> struct SlotArgs {
 };
 
 template <typename T, int NC, class Pro>
-__global__ void __launch_bounds__(512) k_x_fwd_b(Geom g, SlotArgs<Pro> args,
+__global__ void __launch_bounds__(x_max_threads<T>(), x_min_blocks<T>()) k_x_fwd_b(Geom g, SlotArgs<Pro> args,
                                                  const typename cplx_of<T>::type *__restrict__ tw) {
     typedef typename cplx_of<T>::type C;
     const SlotArg<Pro> &a = args.a[blockIdx.z];
@@ -193,14 +199,14 @@ __device__ __forceinline__ void x_inv_body(const Geom &g, const typename cplx_of
 }
 
 template <typename T, int NC, class Epi>
-__global__ void __launch_bounds__(512) k_x_inv(Geom g, const typename cplx_of<T>::type *__restrict__ spec, Epi epi,
+__global__ void __launch_bounds__(x_max_threads<T>(), x_min_blocks<T>()) k_x_inv(Geom g, const typename cplx_of<T>::type *__restrict__ spec, Epi epi,
                                                const typename cplx_of<T>::type *__restrict__ tw, double *partials,
                                                Scal *sc) {
     x_inv_body<T, NC>(g, spec, epi, tw, partials, sc);
 }
 
 template <typename T, int NC, class Epi>
-__global__ void __launch_bounds__(512) k_x_inv_b(Geom g, SlotArgs<Epi> args,
+__global__ void __launch_bounds__(x_max_threads<T>(), x_min_blocks<T>()) k_x_inv_b(Geom g, SlotArgs<Epi> args,
                                                  const typename cplx_of<T>::type *__restrict__ tw) {
     typedef typename cplx_of<T>::type C;
     const SlotArg<Epi> &a = args.a[blockIdx.z];
@@ -267,13 +273,13 @@ __device__ __forceinline__ void x_mid_body(const Geom &g, typename cplx_of<T>::t
 }
 
 template <typename T, int NCI, int NCO, class Mid>
-__global__ void __launch_bounds__(512) k_x_mid(Geom g, typename cplx_of<T>::type *__restrict__ spec, Mid mid,
+__global__ void __launch_bounds__(x_max_threads<T>(), x_min_blocks<T>()) k_x_mid(Geom g, typename cplx_of<T>::type *__restrict__ spec, Mid mid,
                                                const typename cplx_of<T>::type *__restrict__ tw, Scal *sc) {
     x_mid_body<T, NCI, NCO>(g, spec, mid, tw, sc);
 }
 
 template <typename T, int NCI, int NCO, class Mid>
-__global__ void __launch_bounds__(512) k_x_mid_b(Geom g, SlotArgs<Mid> args,
+__global__ void __launch_bounds__(x_max_threads<T>(), x_min_blocks<T>()) k_x_mid_b(Geom g, SlotArgs<Mid> args,
                                                  const typename cplx_of<T>::type *__restrict__ tw) {
     typedef typename cplx_of<T>::type C;
     const SlotArg<Mid> &a = args.a[blockIdx.z];
