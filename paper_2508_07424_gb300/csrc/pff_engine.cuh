@@ -1161,9 +1161,9 @@ struct Engine : EngineBase {
         g_last_error = what;
         return code;
     }
-    // x passes of the FP32 path: the shared-memory carveout at its maximum, so that shared memory
-    // does not cap the resident CTAs below what their register bound allows (L1 caching does not
-    // help these streaming passes)
+    // forward x pass of the FP32 path: the shared-memory carveout at its maximum, so that shared
+    // memory does not cap the resident CTAs below what its register bound allows (L1 caching does
+    // not help its streaming prologue)
     template <typename K> void prep_x(K kernel, size_t bytes) {
         prep_smem(kernel, bytes);
         if (sizeof(T) != 4 || carveout_set.count((const void *)kernel)) return;
@@ -1279,7 +1279,7 @@ struct Engine : EngineBase {
     template <int NC, class Epi, typename U = T> void x_inv(const Epi &epi, Scal *s) {
         int th, bl; size_t sm; xcfg<U>(th, bl, sm);
         auto k = k_x_inv<U, NC, Epi>;
-        prep_x(k, sm * NC);
+        prep_smem(k, sm * NC);
         cudaEvent_t e = tbeg(std::is_same<U, T>::value ? 3 : 7, is_cg_epi<Epi>::value ? 3 : 0,
                              xbytes<U>(NC, rw_words<Epi>()), xflops(NC));
         k<<<bl, th, sm * NC, st>>>(g, spec_of<U>(), epi, tw_of<U>(g.nx), partials, s);
@@ -1291,7 +1291,7 @@ struct Engine : EngineBase {
     template <int NCI, int NCO, class Mid> void x_mid2(const Mid &mid, Scal *s) {
         int th, bl; size_t sm; xcfg(th, bl, sm);
         auto k = k_x_mid<T, NCI, NCO, Mid>;
-        prep_x(k, sm * NCI);
+        prep_smem(k, sm * NCI);
         cudaEvent_t e = tbeg(4, 0, xbytes(NCI + NCO, rw_words<Mid>()), xflops(NCI + NCO));
         k<<<bl, th, sm * NCI, st>>>(g, spec, mid, tw[g.nx], s);
         CK(cudaGetLastError());
@@ -1400,7 +1400,7 @@ struct Engine : EngineBase {
                  cudaStream_t s) {
         int th, bl; size_t sm; xcfg(th, bl, sm);
         auto k = k_x_inv_b<T, NC, Epi>;
-        prep_x(k, sm * NC);
+        prep_smem(k, sm * NC);
         k<<<dim3(bl, 1, (unsigned)es.size()), th, sm * NC, s>>>(g, slot_args(es, fs, scs), tw[g.nx]);
     }
     template <int NCI, int NCO, class Mid>
@@ -1408,7 +1408,7 @@ struct Engine : EngineBase {
                  cudaStream_t s) {
         int th, bl; size_t sm; xcfg(th, bl, sm);
         auto k = k_x_mid_b<T, NCI, NCO, Mid>;
-        prep_x(k, sm * NCI);
+        prep_smem(k, sm * NCI);
         k<<<dim3(bl, 1, (unsigned)es.size()), th, sm * NCI, s>>>(g, slot_args(es, fs, scs), tw[g.nx]);
     }
     template <int NCI, int NCO, int MODE, class Op>

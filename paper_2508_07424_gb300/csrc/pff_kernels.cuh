@@ -28,9 +28,10 @@ enum { AX_FWD = 0, AX_INV = 1, AX_FWD_OP_INV = 2 };
 template <class E, class = void> struct facc_of : std::false_type {};
 template <class E> struct facc_of<E, std::void_t<decltype(E::FACC)>> : std::integral_constant<bool, E::FACC> {};
 
-// Launch bounds of the x passes: at most 256 threads (max(128, nx / 4)); on the FP32 path at
-// least 3 such CTAs per SM (<= 85 registers), so that more warps cover the latency of the fused
-// pointwise loads, which bound the FP32 x passes of large grids.
+// Launch bounds of the forward x pass: at most 256 threads (max(128, nx / 4)); on the FP32 path
+// at least 3 such CTAs per SM (<= 85 registers), so that more warps cover the latency of the
+// fused prologue's loads, which bound it on large grids (128^3: 174 -> 150 us per CG launch;
+// the inverse and middle x passes measured 5-10 % slower with the same bound and keep theirs).
 template <typename T> __host__ __device__ constexpr int x_max_threads() { return sizeof(T) == 4 ? 256 : 512; }
 template <typename T> __host__ __device__ constexpr int x_min_blocks() { return sizeof(T) == 4 ? 3 : 1; }
 
@@ -199,14 +200,14 @@ __device__ __forceinline__ void x_inv_body(const Geom &g, const typename cplx_of
 }
 
 template <typename T, int NC, class Epi>
-__global__ void __launch_bounds__(x_max_threads<T>(), x_min_blocks<T>()) k_x_inv(Geom g, const typename cplx_of<T>::type *__restrict__ spec, Epi epi,
+__global__ void __launch_bounds__(512) k_x_inv(Geom g, const typename cplx_of<T>::type *__restrict__ spec, Epi epi,
                                                const typename cplx_of<T>::type *__restrict__ tw, double *partials,
                                                Scal *sc) {
     x_inv_body<T, NC>(g, spec, epi, tw, partials, sc);
 }
 
 template <typename T, int NC, class Epi>
-__global__ void __launch_bounds__(x_max_threads<T>(), x_min_blocks<T>()) k_x_inv_b(Geom g, SlotArgs<Epi> args,
+__global__ void __launch_bounds__(512) k_x_inv_b(Geom g, SlotArgs<Epi> args,
                                                  const typename cplx_of<T>::type *__restrict__ tw) {
     typedef typename cplx_of<T>::type C;
     const SlotArg<Epi> &a = args.a[blockIdx.z];
@@ -273,13 +274,13 @@ __device__ __forceinline__ void x_mid_body(const Geom &g, typename cplx_of<T>::t
 }
 
 template <typename T, int NCI, int NCO, class Mid>
-__global__ void __launch_bounds__(x_max_threads<T>(), x_min_blocks<T>()) k_x_mid(Geom g, typename cplx_of<T>::type *__restrict__ spec, Mid mid,
+__global__ void __launch_bounds__(512) k_x_mid(Geom g, typename cplx_of<T>::type *__restrict__ spec, Mid mid,
                                                const typename cplx_of<T>::type *__restrict__ tw, Scal *sc) {
     x_mid_body<T, NCI, NCO>(g, spec, mid, tw, sc);
 }
 
 template <typename T, int NCI, int NCO, class Mid>
-__global__ void __launch_bounds__(x_max_threads<T>(), x_min_blocks<T>()) k_x_mid_b(Geom g, SlotArgs<Mid> args,
+__global__ void __launch_bounds__(512) k_x_mid_b(Geom g, SlotArgs<Mid> args,
                                                  const typename cplx_of<T>::type *__restrict__ tw) {
     typedef typename cplx_of<T>::type C;
     const SlotArg<Mid> &a = args.a[blockIdx.z];
