@@ -34,9 +34,10 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 WORKLOAD = "fibre_composite_512"
 METRIC = "FFT-PFF voxel-updates/s"
 
-# DRAM bytes per launch of a kernel class, from ncu captures of this build's kernels (dram__bytes_
-# read.sum + dram__bytes_write.sum averaged over the captured launches), keyed by (workload,
-# precision, kernel class). A class without a capture of its current code reports null.
+# DRAM bytes per launch of a kernel, from ncu captures of the current kernel code (dram__bytes_
+# read.sum + dram__bytes_write.sum of the captured launch), keyed by (workload, precision, kernel
+# class). A kernel without a capture of its current code reports null; an entry is removed when
+# the kernel it describes changes.
 TRAFFIC = {
     ("fibre_composite_512", "fp64", "projection_pass"): 6432256 + 0,
     ("polycrystal_3d_128", "fp32r", "projection_pass"): 56673536 + 2820608,

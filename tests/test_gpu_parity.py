@@ -329,7 +329,7 @@ def test_fp32r_equilibrium_solve(cap):
     assert rel(g.get(cap.RVE_FIELD_PSI1), model.drive(eps)) < 1e-6
 
 
-# ---- spectral energy split (configs[0] model variant; plane strain) ------------------------------
+# ---- spectral energy split (the 64^2 plate's model variant; plane strain) ------------------------------
 def _split_case():
     w = synth.small_cases()["homog32"]
     return synth.replace(w, split=1)
