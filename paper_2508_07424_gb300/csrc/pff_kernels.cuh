@@ -522,7 +522,6 @@ template <typename C, int R> __device__ __forceinline__ void regs_dit(C (&v)[R])
 template <typename C, int R>
 __device__ __forceinline__ void wfft2_fwd(C (&v)[R], C *line, int l, int L, const C *__restrict__ tw) {
     constexpr int G = 32 / R, lgR = log2_of<R>::v, rs = 32 + G;
-    typedef typename real_of<C>::type Rt;
     regs_dif<C, R>(v);
 #pragma unroll
     for (int m = 1; m < R; ++m) {
@@ -552,7 +551,6 @@ __device__ __forceinline__ void wfft2_fwd(C (&v)[R], C *line, int l, int L, cons
 template <typename C, int R>
 __device__ __forceinline__ void wfft2_inv(C (&v)[R], C *line, int l, int L, const C *__restrict__ tw) {
     constexpr int G = 32 / R, lgR = log2_of<R>::v, rs = 32 + G;
-    typedef typename real_of<C>::type Rt;
     const int j = l / G, gg = l & (G - 1);
     if (G > 1) {
         lane_stage_inv<C, R, false>(v, l, 1, 0, tw);
